@@ -1,0 +1,148 @@
+"""Pins of oracle/lbm.py: collision invariants, conservation, fixed points, the
+streaming permutation, a naive per-cell brute force, and exact Riemann plateaus."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import lbm, riemann
+from oracle.model import get_model
+from paper_1303_4624_gb300 import workloads as W
+from test_oracle_equilibrium import feq_by_moment_matching
+
+
+def random_state(mdl, shape, seed, amp=0.05):
+    rng = np.random.default_rng(seed)
+    rho = 1.0 + amp * rng.standard_normal(shape)
+    U = 0.05 * rng.standard_normal((mdl.D,) + shape)
+    T = mdl.T0 * (1.0 + amp * rng.standard_normal(shape))
+    S = lbm.init_populations(mdl, rho, U, T)
+    # perturb away from equilibrium so the collision does something
+    S = S * (1.0 + 0.02 * rng.standard_normal(S.shape))
+    return S
+
+
+@pytest.mark.parametrize("name", ["D2Q33", "D3Q95"])
+def test_collision_invariants_per_cell(name):
+    mdl = get_model(name)
+    shape = (3, 4, 5) if mdl.D == 3 else (1, 6, 7)
+    g = random_state(mdl, shape, 1)
+    out = lbm.collide(mdl, g, 1.7)
+    xi = mdl.xi
+    d = (out - g).reshape(mdl.Q, -1)
+    gf = g.reshape(mdl.Q, -1)
+    for weight in [np.ones(mdl.Q)] + [xi[:, k] for k in range(mdl.D)] + [(xi * xi).sum(1)]:
+        scale = np.abs(weight) @ np.abs(gf)
+        assert np.max(np.abs(weight @ d) / scale) < 1e-14
+
+
+@pytest.mark.parametrize("name,shape", [("D2Q33", (1, 5, 7)), ("D3Q95", (4, 5, 6))])
+def test_global_conservation_over_many_steps(name, shape):
+    mdl = get_model(name)
+    S = random_state(mdl, shape, 2)
+    a0 = lbm.audit(mdl, S)
+    S = lbm.run(mdl, S, 1.6, 300)
+    a1 = lbm.audit(mdl, S)
+    # FP64 roundoff accumulates over the 300 steps (about 1e-15 per step)
+    assert abs(a1["mass"] - a0["mass"]) / a0["mass"] < 1e-12
+    assert abs(a1["energy"] - a0["energy"]) / a0["energy"] < 1e-12
+    assert np.max(np.abs(a1["momentum"] - a0["momentum"])) / a0["mass"] < 1e-12
+
+
+@pytest.mark.parametrize("name", ["D2Q33", "D3Q95"])
+def test_rest_and_uniform_flow_are_fixed_points(name):
+    mdl = get_model(name)
+    shape = (3, 4, 5) if mdl.D == 3 else (1, 4, 6)
+    for U0 in (0.0, 0.07):
+        rho = np.full(shape, 0.8)
+        U = np.zeros((mdl.D,) + shape)
+        U[0] = U0
+        T = np.full(shape, 1.1 * mdl.T0)
+        S = lbm.init_populations(mdl, rho, U, T)
+        S2 = lbm.run(mdl, S, 1.5, 200)
+        r, u, t = lbm.macroscopic(mdl, S2)
+        # roundoff over 200 steps
+        assert np.max(np.abs(r - 0.8)) < 1e-12
+        assert np.max(np.abs(u[0] - U0)) < 1e-12 and np.max(np.abs(u[1:])) < 1e-12
+        assert np.max(np.abs(t / mdl.T0 - 1.1)) < 1e-12
+        assert np.max(np.abs(S2 - S)) < 1e-12
+
+
+@pytest.mark.parametrize("name,shape", [("D2Q33", (1, 3, 7)), ("D3Q95", (2, 3, 4)), ("D3Q95", (7, 1, 11))])
+def test_streaming_permutation_integer_labels(name, shape):
+    """Pull streaming with omega = 0 moves label(x) to x + n e_i, true modulo, bit for bit.
+    The expected labels are computed with explicit index arithmetic, not np.roll."""
+    mdl = get_model(name)
+    nz, ny, nx = shape
+    Q = mdl.Q
+    idx = np.arange(nz * ny * nx, dtype=np.float64).reshape(shape)
+    S = np.stack([idx + 1000.0 * i + 1.0 for i in range(Q)])
+    n = 3
+    out = S.copy()
+    for _ in range(n):
+        out = lbm.step(mdl, out, 0.0)
+    for i in range(Q):
+        e = mdl.e[i]
+        ex, ey = int(e[0]), int(e[1])
+        ez = int(e[2]) if mdl.D == 3 else 0
+        for z in range(nz):
+            for y in range(ny):
+                for x in range(nx):
+                    sx, sy, sz = (x - n * ex) % nx, (y - n * ey) % ny, (z - n * ez) % nz
+                    assert out[i, z, y, x] == (sz * ny + sy) * nx + sx + 1000.0 * i + 1.0
+
+
+@pytest.mark.parametrize("name,shape", [("D2Q33", (1, 3, 5)), ("D3Q95", (2, 3, 4))])
+def test_naive_brute_force_step(name, shape):
+    """A naive per-cell loop (modulo indexing, moment sums, linear-solve
+    equilibrium, BGK) agrees with the oracle to 1e-13 on grids smaller than the reach."""
+    mdl = get_model(name)
+    S = random_state(mdl, shape, 3)
+    omega = 1.3
+    ref = lbm.step(mdl, S, omega)
+    nz, ny, nx = shape
+    xi = mdl.xi
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                g = np.empty(mdl.Q)
+                for i in range(mdl.Q):
+                    e = mdl.e[i]
+                    ez = int(e[2]) if mdl.D == 3 else 0
+                    g[i] = S[i, (z - ez) % nz, (y - int(e[1])) % ny, (x - int(e[0])) % nx]
+                rho = g.sum()
+                u = (g @ xi) / rho
+                theta = ((g @ (xi * xi).sum(1)) / rho - u @ u) / mdl.D
+                fe = feq_by_moment_matching(mdl, rho, u, theta)
+                new = (1 - omega) * g + omega * fe
+                assert np.max(np.abs(new - ref[:, z, y, x])) < 1e-13
+
+
+@pytest.mark.parametrize("name,nx,steps", [("D3Q95", 1600, 100), ("D2Q33", 1000, 150)])
+def test_riemann_plateaus(name, nx, steps):
+    """The paper's shock tube states rho = p = 4 | 1, theta = 1, omega = 1.5
+    (paragraph before Figure 1) on a quasi-1D periodic tube: density and
+    temperature on both plateaus match the exact Riemann solution to 0.5 %."""
+    mdl = get_model(name)
+    gam = (mdl.D + 2.0) / mdl.D
+    f = W.riemann_planar(mdl.D, nx, 1, 1, nx // 2, (4.0, 1.0), (1.0, 1.0), noise=0)
+    S = lbm.init_populations(mdl, f.rho, f.U, f.theta * mdl.T0)
+    S = lbm.run(mdl, S, 1.5, steps)
+    rho, U, T = lbm.macroscopic(mdl, S)
+    r, th = rho[0, 0], T[0, 0] / mdl.T0
+    T0 = mdl.T0
+    st = riemann.star_state(4.0, 0.0, 4.0 * T0, 1.0, 0.0, T0, gam)
+    ws = riemann.wave_speeds(4.0, 0.0, 4.0 * T0, 1.0, 0.0, T0, gam)
+    xc = np.arange(nx) + 0.5 - nx // 2
+
+    def central(a, b):
+        L = b - a
+        return (xc > a + 0.3 * L) & (xc < b - 0.3 * L)
+
+    mL = central(ws["left_tail"] * steps, ws["contact"] * steps)
+    mR = central(ws["contact"] * steps, ws["right"] * steps)
+    assert mL.sum() > 20 and mR.sum() > 20
+    assert abs(r[mL].mean() / st.rho_L - 1) < 5e-3
+    assert abs(r[mR].mean() / st.rho_R - 1) < 5e-3
+    assert abs(th[mL].mean() / (st.p / st.rho_L / T0) - 1) < 5e-3
+    assert abs(th[mR].mean() / (st.p / st.rho_R / T0) - 1) < 5e-3
