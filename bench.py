@@ -1,0 +1,446 @@
+"""Benchmark of the D3Q95 thermal BGK stream-collide on one GB300 (or N replicas).
+
+Default workload: D3Q95, FP32 populations, 128 x 64 x 64 periodic box, omega 1.6,
+planar Riemann initial state (seeded).  One bench "step" is one lattice time
+step over the whole grid (one fused stream-collide launch).  The population
+arrays (2 x 199 MB) are larger than the 129 MB L2, so no L2 flush is needed
+between steps.
+
+Prints one JSON line.  value = million lattice-cell updates per second (MLUPS)
+over all ranks; roofline = algorithmic bytes (2 Q s per cell update) per launch
+over the CUDA-event time of a launch, against the measured HBM copy bandwidth.
+Secondary measurements in the same line: the FP32 / FP16 / BF16 storage forms on
+the 512 x 256 x 256 precision-sweep grid, the cost of the adjoint relative to the
+forward on the 128^3 adjoint workload, an end-to-end run through the public API
+from host buffers, and the FP64 oracle timed on the host cores (cpu_baseline).
+
+--impl reference times the FP64 CPU oracle (there is no reference program) on a
+bounded sample of the same workload and prints the same JSON keys.
+
+Multi-GPU (torchrun, N > 1): every rank runs an independent replica of the
+workload (the path has no multi-GPU decomposition here: replicas only, weak
+scaling); the time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "D3Q95 MLUPS and % of HBM roofline; FP16 vs FP32 form at stated error; adjoint cost"
+BYTES = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16", "fp64"])
+    p.add_argument("--grid", default="128x64x64", help="NXxNYxNZ of the D3Q95 Riemann workload")
+    p.add_argument("--no-extras", action="store_true", help="skip the forms / adjoint / cpu legs")
+    return p.parse_args(argv)
+
+
+# ------------------------------------------------------------------ distributed helpers
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def reduce_max_sum(elapsed_s, units, backend_device=None):
+    """(max elapsed over ranks, sum of units over ranks); identity when not distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return elapsed_s, units
+    dev = backend_device or torch.device("cpu")
+    t = torch.tensor([elapsed_s], dtype=torch.float64, device=dev)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), u.item()
+
+
+# ------------------------------------------------------------------ peaks, clocks, profiles
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        rows = [r.split(",") for r in out.strip().splitlines() if r.count(",") >= 8]
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if r[5 + k].strip().lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for fn in ("kernels.cuh", "velset.cuh", "k_storage.inl", "common.h"):
+        with open(os.path.join(ROOT, "paper_1303_4624_gb300", "csrc", fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload_key):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the
+    current kernel source (its 'source_hash' line matches); else None."""
+    d = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(d):
+        return None
+    src = kernel_source_hash()
+    for fn in sorted(os.listdir(d)):
+        if not fn.endswith(".md"):
+            continue
+        with open(os.path.join(d, fn)) as f:
+            text = f.read()
+        m_hash = re.search(r"source_hash:\s*([0-9a-f]+)", text)
+        m_key = re.search(r"workload_key:\s*(\S+)", text)
+        m_tr = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+        if m_hash and m_key and m_tr and m_hash.group(1) == src and m_key.group(1) == workload_key:
+            return float(m_tr.group(1))
+    return None
+
+
+# ------------------------------------------------------------------ our arm
+def time_steps(lbm, lat, steps, warmup, stream):
+    import torch
+    lbm.lbm_step(lat.ctx, warmup)
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    lbm.lbm_step(lat.ctx, steps)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    return start.elapsed_time(stop) / 1e3
+
+
+def make_lattice(lbm, wl, fields, storage=None):
+    lat = lbm.Lattice(wl.model, wl.dims, wl.omega, storage or wl.storage)
+    lat.init(fields.rho, fields.U, fields.theta * lat.info["T0"])
+    return lat
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1303_4624_gb300 import lbm
+    from paper_1303_4624_gb300 import workloads as W
+
+    stream = torch.cuda.current_stream()
+    nx, ny, nz = (int(v) for v in args.grid.lower().split("x"))
+    wl, fields = W.d3q95_riemann(nx, ny, nz, storage=args.storage)
+    Q = lbm.lbm_model_info(wl.model)["Q"]
+    lat = make_lattice(lbm, wl, fields)
+    launches0 = lbm.lbm_launch_count(lat.ctx)
+
+    # ---- timed region: K fused stream-collide launches on the resident state
+    lbm.lbm_step(lat.ctx, args.warmup)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    time.sleep(0.15)
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    lbm.lbm_step(lat.ctx, args.steps)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    elapsed = start.elapsed_time(stop) / 1e3
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    gpu_launches = lbm.lbm_launch_count(lat.ctx) - launches0 - args.warmup
+    t_max, units = reduce_max_sum(elapsed, wl.cells * args.steps,
+                                  torch.device("cuda", local) if world > 1 else None)
+    audit = lat.audit()
+    value = units / t_max / 1e6
+    per_launch = elapsed / args.steps
+    alg_bytes = wl.cells * 2 * Q * BYTES[wl.storage]
+    achieved = alg_bytes / per_launch / 1e9
+    peak, peak_kind = hbm_peak()
+    line = {
+        "metric": METRIC,
+        "value": round(value, 1),
+        "unit": "MLUPS",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(t_max / args.steps * 1e3, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if wl.storage == "fp64" else "f32",
+        "data": "synthetic (seeded planar Riemann state, SplitMix64 noise)",
+        "config": {"workload": wl.name, "model": "D3Q95",
+                   "storage": "%s (deviation h = f/w - 1)" % wl.storage,
+                   "grid": "%dx%dx%d" % wl.dims, "omega": wl.omega, "cells": wl.cells,
+                   "l2": "inputs larger than L2 (2 x %.0f MB state vs 129 MB L2)"
+                         % (wl.cells * Q * BYTES[wl.storage] / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"
+                     if peak_kind == "measured" else "fallback 6.8 TB/s",
+                     "traffic": profiled_traffic("d3q95_%s_%dx%dx%d" % ((wl.storage,) + wl.dims)),
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "launch_ms": round(per_launch * 1e3, 5)},
+        "clocks": clk,
+        "gpu_launches": int(gpu_launches),
+        "audit_after": {"nonfinite": audit["nonfinite"], "mass": audit["mass"]},
+    }
+    if rank == 0 and not args.no_extras:
+        line["e2e"] = e2e_leg(lbm, W, wl, fields, args.steps, stream)
+        line["forms"] = forms_leg(lbm, W, stream)
+        line["adjoint"] = adjoint_leg(lbm, W, stream)
+        line["cpu_baseline"] = cpu_baseline_leg()
+    lat.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def e2e_leg(lbm, W, wl, fields, steps, stream):
+    """Whole job through the public API from pinned host buffers: lbm_init from
+    host fields, `steps` steps, lbm_moments back to host; timed on the host clock."""
+    import numpy as np
+    import torch
+    D = 3
+    rho = torch.from_numpy(fields.rho).pin_memory().numpy()
+    U = torch.from_numpy(np.ascontiguousarray(fields.U)).pin_memory().numpy()
+    lat = lbm.Lattice(wl.model, wl.dims, wl.omega, wl.storage)
+    T = torch.from_numpy(fields.theta * lat.info["T0"]).pin_memory().numpy()
+    out_r = torch.empty(fields.rho.shape, dtype=torch.float64).pin_memory().numpy()
+    out_U = torch.empty((D,) + fields.rho.shape, dtype=torch.float64).pin_memory().numpy()
+    out_T = torch.empty(fields.rho.shape, dtype=torch.float64).pin_memory().numpy()
+    lat.init(rho, U, T)   # warm-up of the path
+    lbm.lbm_moments(lat.ctx, out_r, out_U, out_T)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lat.init(rho, U, T)
+    lat.step(steps)
+    lbm.lbm_moments(lat.ctx, out_r, out_U, out_T)
+    dt = time.perf_counter() - t0
+    lat.close()
+    h2d = rho.nbytes + U.nbytes + T.nbytes
+    d2h = out_r.nbytes + out_U.nbytes + out_T.nbytes
+    return {"value": round(wl.cells * steps / dt / 1e6, 1), "unit": "MLUPS",
+            "h2d_bytes_per_step": round(h2d / steps, 1), "d2h_bytes_per_step": round(d2h / steps, 1),
+            "note": "one lbm_init from host fields + %d steps + lbm_moments to host, host clock" % steps}
+
+
+def forms_leg(lbm, W, stream, steps=200):
+    """FP32 vs FP16 / BF16 deviation storage on the 512 x 256 x 256 precision-sweep grid."""
+    import torch
+    out = {"grid": "512x256x256", "steps": steps, "omega": 1.8}
+    for st in ("fp32", "fp16", "bf16"):
+        wl, fields = W.d3q95_sweep(storage=st)
+        lat = make_lattice(lbm, wl, fields)
+        dt = time_steps(lbm, lat, steps, 5, stream)
+        Q = lat.info["Q"]
+        mlups = wl.cells * steps / dt / 1e6
+        out[st] = {"mlups": round(mlups, 1),
+                   "gbs": round(wl.cells * 2 * Q * BYTES[st] / (dt / steps) / 1e9, 1)}
+        lat.close()
+        del fields
+        torch.cuda.empty_cache()
+    out["fp16_over_fp32"] = round(out["fp16"]["mlups"] / out["fp32"]["mlups"], 3)
+    out["bf16_over_fp32"] = round(out["bf16"]["mlups"] / out["fp32"]["mlups"], 3)
+    out["error_vs_fp64_oracle"] = ("measured by tests/test_gpu_precision.py on the 128x32x32 "
+                                   "run of the identical setup (200 steps)")
+    return out
+
+
+def adjoint_leg(lbm, W, stream, n=128, steps=500, k=22):
+    """Cost of lbm_backward (replay + adjoint) over lbm_record (checkpointed forward)."""
+    import numpy as np
+    import torch
+    wl, fields = W.d3q95_adjoint(n)
+    lat = lbm.Lattice(wl.model, wl.dims, wl.omega, "fp32")
+    lat.init(fields.rho, fields.U, fields.theta * lat.info["T0"])
+    g = torch.zeros(fields.rho.shape, dtype=torch.float64, device="cuda")
+    g += 1.0 / fields.rho.size
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    lbm.lbm_record(lat.ctx, 20, 5)       # warm-up (allocations)
+    lbm.lbm_backward(lat.ctx, g)
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    lbm.lbm_record(lat.ctx, steps, k)
+    ev[1].record(stream)
+    lbm.lbm_backward(lat.ctx, g)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    fwd = ev[0].elapsed_time(ev[1]) / 1e3
+    bwd = ev[1].elapsed_time(ev[2]) / 1e3
+    lbm.lbm_release_record(lat.ctx)
+    lat.close()
+    torch.cuda.empty_cache()
+    return {"workload": wl.name, "steps": steps, "ckpt_every": k, "forward_s": round(fwd, 4),
+            "backward_s": round(bwd, 4), "backward_over_forward": round(bwd / fwd, 3),
+            "forward_mlups": round(wl.cells * steps / fwd / 1e6, 1)}
+
+
+CPU_SAMPLE = """
+import json, os, sys, time
+sys.path.insert(0, %r)
+from oracle import lbm
+from oracle.model import get_model
+from paper_1303_4624_gb300 import workloads as W
+mdl = get_model("D3Q95")
+wl, f = W.d3q95_riemann(nx=128, ny=%d, nz=%d)
+S = lbm.init_populations(mdl, f.rho, f.U, f.theta * mdl.T0)
+S = lbm.step(mdl, S, wl.omega)
+n = 0
+t0 = time.perf_counter()
+while True:
+    S = lbm.step(mdl, S, wl.omega)
+    n += 1
+    dt = time.perf_counter() - t0
+    if n >= %d or dt > %f:
+        break
+print(json.dumps({"steps": n, "seconds": dt, "cells": wl.cells}))
+"""
+
+
+def run_oracle_sample(ny, nz, max_steps, budget_s):
+    env = dict(os.environ)
+    cores = os.cpu_count() or 1
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(cores)
+    code = CPU_SAMPLE % (ROOT, ny, nz, max_steps, budget_s)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=budget_s * 4 + 120)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    res["cores"] = cores
+    return res
+
+
+def cpu_baseline_leg():
+    res = run_oracle_sample(32, 16, 10 ** 9, 15.0)
+    return {"value": round(res["cells"] * res["steps"] / res["seconds"] / 1e6, 4), "unit": "MLUPS",
+            "cores": res["cores"], "kind": "oracle",
+            "sample": "FP64 numpy oracle, D3Q95 planar Riemann 128x32x16 sub-box (same setup), "
+                      "%d steps in %.1f s, BLAS threads = cores" % (res["steps"], res["seconds"])}
+
+
+# ------------------------------------------------------------------ reference arm (the oracle)
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    total = args.steps + args.warmup
+    # size the sample so the whole run stays within ~2 minutes (oracle ~1e-5 s per cell update)
+    budget = 120.0
+    cells = max(128, min(128 * 64 * 64, int(budget / (total * 1.2e-5))))
+    ny = nz = max(1, int(math.sqrt(cells / 128)))
+    res = run_oracle_sample(ny, nz, total, budget * 1.5)
+    value = res["cells"] * res["steps"] / res["seconds"] / 1e6
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": round(value, 4),
+        "unit": "MLUPS",
+        "n_gpus": world,
+        "steps": res["steps"],
+        "warmup": 0,
+        "ms_per_step": round(res["seconds"] / res["steps"] * 1e3, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded planar Riemann state)",
+        "config": {"workload": "d3q95_riemann_128x64x64", "model": "D3Q95", "grid": "128x64x64",
+                   "omega": 1.6},
+        "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": res["cores"],
+                         "kind": "oracle",
+                         "sample": "FP64 numpy oracle on a 128x%dx%d sub-box of the same setup, "
+                                   "%d steps" % (ny, nz, res["steps"])},
+        "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

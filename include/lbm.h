@@ -1,0 +1,221 @@
+/*
+ * lbm.h - C ABI of the GB300 thermal lattice Boltzmann library (liblbm_gb300.so).
+ *
+ * The library implements the fused pull stream-and-collide BGK update of
+ * J. W. Shim, "Multidimensional On-lattice Higher-order Models in the Thermal
+ * Lattice Boltzmann Theory" (arXiv:1303.4624), on the paper's fourth-order
+ * on-lattice velocity sets D2Q33 (Table 2) and D3Q95 (Table 3), on one GPU.
+ *
+ * Conventions shared by every entry point
+ *   - Lattice units: V_i = e_i (integer lattice vectors), dx = dt = 1,
+ *     k_B/m_g = 1.  The paper's dimensionless variables (text after the
+ *     Maxwellian) map to these by v = c V, u = c U and theta = T / T0 with
+ *     T0 = 1 / (2 c^2), where c is the model's speed scale of Table 2 / 3.
+ *   - Grids are periodic boxes of Nx x Ny x Nz cells (Nz = 1 for D2Q33).
+ *     Every field array is x-fastest: index = (z * Ny + y) * Nx + x.
+ *     A vector field U is [D][cells] (component-major).  Population arrays
+ *     are [Q][cells] in the direction order reported by lbm_model_info.
+ *   - Time stepping is the pull form of the paper's update
+ *       f_i(x + V_i, t + 1) = (1 - omega) f_i(x, t) + omega f_i^eq(x, t):
+ *     each step gathers g_i(x) = f_i(x - e_i) and stores the post-collision
+ *     populations at x.  rho, U and T are the same as in the push form.
+ *   - f_i^eq is the fourth-order Hermite expansion of the Maxwellian about
+ *     (u = 0, theta = 1) on the model's weights (Formula 1 with m = N = 4).
+ *   - `where` arguments: LBM_HOST for host pointers, LBM_DEVICE for device
+ *     pointers on the context's device.  Caller buffers are borrowed only for
+ *     the duration of the call; the library keeps no pointer to them.
+ *   - All calls are ordered on the context's CUDA stream.  Calls that take a
+ *     host output return after the result is on the host; calls with device
+ *     outputs (and lbm_step) return after enqueueing.
+ *   - Every call returns LBM_OK (0) or a negative error code; arguments are
+ *     validated on the host before anything is launched.  lbm_last_error()
+ *     gives a message for the most recent failure on the calling thread.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ---- */
+#define LBM_OK         0
+#define LBM_EINVAL    -1   /* invalid argument (checked before any launch)          */
+#define LBM_ENOMEM    -2   /* device allocation failed                              */
+#define LBM_ECUDA     -3   /* a CUDA runtime call or kernel launch failed            */
+#define LBM_EUNSTABLE -4   /* the audit found non-finite populations                */
+#define LBM_ESTATE    -5   /* call out of order (e.g. lbm_step before lbm_init)      */
+
+/* ---- models and storage forms ---- */
+#define LBM_D2Q33 0        /* Table 2: 33 velocities, 8 groups, reach 4 */
+#define LBM_D3Q95 1        /* Table 3: 95 velocities, 10 groups, reach 5 */
+
+#define LBM_FP64    0      /* populations stored in FP64, FP64 arithmetic              */
+#define LBM_FP32    1      /* FP32 storage and arithmetic                              */
+#define LBM_FP16DEV 2      /* FP16 storage of h_i = f_i / w_i - 1, FP32 arithmetic     */
+#define LBM_BF16DEV 3      /* BF16 storage of h_i = f_i / w_i - 1, FP32 arithmetic     */
+/* Every form stores the deviation h_i = f_i / w_i - 1 from the rest state
+ * (rho0 = 1, U = 0, T = T0, where f_i^eq = w_i exactly), so all directions
+ * share one dynamic range.  In the FP32 / FP16 / BF16 forms the moment sums for
+ * density and energy are Kahan-compensated FP32 and the temperature
+ * theta = (E / rho - |u|^2) / D is recovered in FP64. */
+
+#define LBM_HOST   0
+#define LBM_DEVICE 1
+
+typedef struct lbm_ctx lbm_ctx;     /* opaque; owns the device population buffers */
+
+/*
+ * lbm_model_info - the velocity set and weights of a model.
+ *   Tables 2 and 3 give one representative velocity per symmetry group; the
+ *   set is every signed permutation of each representative (text before
+ *   Formula 9).  The weights and c are the FP64 solution of Formula 5 up to
+ *   n_max = 8, found by Newton's method from the printed values.
+ *   Direction order: 0 is the rest velocity, then opposite pairs
+ *   (2p+1, 2p+2) with e_{2p+2} = -e_{2p+1}.
+ * Outputs (any may be NULL): Q, D, reach (max |e_i| component), e [Q*D] as
+ *   int32 (x fastest within a direction), w [Q], c, T0 (lattice units).
+ * Errors: LBM_EINVAL for an unknown model; LBM_ECUDA never.
+ */
+int lbm_model_info(int model, int* Q, int* D, int* reach, int32_t* e, double* w,
+                   double* c, double* T0);
+
+/*
+ * lbm_set_allocator - route the library's device allocations through the
+ * caller (the Python binding passes PyTorch's caching allocator).  alloc
+ * returns a device pointer of at least `bytes` bytes or NULL; free releases it.
+ * Both receive the stream of the context that allocates and `user`.  Passing
+ * NULL functions restores cudaMalloc / cudaFree.  Affects later allocations
+ * only; each buffer is released by the allocator that made it.
+ */
+typedef void* (*lbm_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*lbm_free_fn)(void* ptr, void* stream, void* user);
+int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn free_fn, void* user);
+
+/*
+ * lbm_create - allocate a context for one periodic grid on the current device.
+ *   model:   LBM_D2Q33 or LBM_D3Q95
+ *   dims:    {Nx, Ny, Nz}, each >= 1, Nz == 1 for D2Q33; Nx*Ny*Nz < 2^31
+ *   omega:   BGK relaxation frequency (the paper's omega), 0 <= omega < 2
+ *   storage: LBM_FP64 / LBM_FP32 / LBM_FP16DEV / LBM_BF16DEV
+ *   stream:  cudaStream_t to order all work on (NULL = legacy default stream)
+ * Allocates two population buffers (ping-pong) of Q * cells storage elements.
+ * Errors: LBM_EINVAL (bad argument), LBM_ENOMEM, LBM_ECUDA.
+ */
+int lbm_create(lbm_ctx** out, int model, const int64_t dims[3], double omega,
+               int storage, void* stream);
+
+/* lbm_destroy - free every buffer of the context (after its stream drains). */
+int lbm_destroy(lbm_ctx* ctx);
+
+/* lbm_set_omega - change the relaxation frequency (0 <= omega < 2) for later
+ * steps; invalidates a recorded rollout.  Errors: LBM_EINVAL. */
+int lbm_set_omega(lbm_ctx* ctx, double omega);
+
+/* lbm_set_stream - order later calls on another stream of the same device. */
+int lbm_set_stream(lbm_ctx* ctx, void* stream);
+
+/*
+ * lbm_init - set every cell to the discrete equilibrium f_i^eq(rho, U, T).
+ *   rho [cells], U [D][cells] (lattice units), T [cells] (lattice units),
+ *   all FP64 in `where` memory.  rho > 0 and T > 0 and all values finite
+ *   (checked on the host for LBM_HOST; for LBM_DEVICE inputs the values are
+ *   not inspected).  The fields are also kept on the device as the initial
+ *   state of the differentiable rollout (lbm_record / lbm_backward).
+ * Errors: LBM_EINVAL, LBM_ECUDA.
+ */
+int lbm_init(lbm_ctx* ctx, const double* rho, const double* U, const double* T, int where);
+
+/*
+ * lbm_step - advance n >= 0 time steps (one fused stream-collide launch each).
+ * Enqueues and returns.  Errors: LBM_ESTATE before lbm_init, LBM_EINVAL, LBM_ECUDA.
+ */
+int lbm_step(lbm_ctx* ctx, int64_t n);
+
+/* lbm_steps_done - number of steps taken since the last lbm_init / set. */
+int64_t lbm_steps_done(const lbm_ctx* ctx);
+
+/*
+ * lbm_moments - macroscopic fields of the current state (Formula 1, n <= 2):
+ *   rho = sum f_i, rho U = sum f_i e_i, D rho T = sum f_i |e_i - U|^2,
+ *   computed in FP64 from the stored populations.  Outputs rho [cells],
+ *   U [D][cells], T [cells] in `where` memory; any output may be NULL.
+ * Errors: LBM_ESTATE, LBM_EINVAL, LBM_ECUDA.
+ */
+int lbm_moments(lbm_ctx* ctx, double* rho, double* U, double* T, int where);
+
+/*
+ * lbm_audit - conservation audit of the current state, FP64, deterministic
+ * (fixed reduction order).  out[8] (host) receives:
+ *   [0] mass = sum_x sum_i f_i        [1..3] momentum sum f_i e_i (zero-padded)
+ *   [4] energy = sum f_i |e_i|^2 / 2  [5] min over populations of f_i / w_i
+ *   [6] number of non-finite populations  [7] number of cells
+ * Returns LBM_EUNSTABLE (after filling out) if any population is non-finite.
+ */
+int lbm_audit(lbm_ctx* ctx, double out[8]);
+
+/*
+ * lbm_get_populations / lbm_set_populations - the state as physical FP64
+ * populations f [Q][cells] (f_i = w_i (1 + h_i)).  set encodes to the storage
+ * form (round to nearest even) and resets the step counter.
+ */
+int lbm_get_populations(lbm_ctx* ctx, double* f, int where);
+int lbm_set_populations(lbm_ctx* ctx, const double* f, int where);
+
+/*
+ * lbm_get_raw / lbm_set_raw - the stored deviations h [Q][cells] bit for bit
+ * in the storage type (8, 4, 2 or 2 bytes per element); bytes = Q*cells*size.
+ * Used for the integer-label streaming check and for saving / restoring state.
+ */
+int lbm_get_raw(lbm_ctx* ctx, void* h, size_t bytes, int where);
+int lbm_set_raw(lbm_ctx* ctx, const void* h, size_t bytes, int where);
+
+/*
+ * lbm_record - the forward half of the differentiable rollout
+ * (rho0, U0, T0, omega) -> state after nsteps.  Re-initialises from the
+ * fields of the last lbm_init, runs nsteps >= 1 steps, and keeps every
+ * ckpt_every-th state (1 <= ckpt_every) as a checkpoint for lbm_backward.
+ * Checkpoint memory: ceil(nsteps / ckpt_every) states.
+ * Errors: LBM_ESTATE (no lbm_init), LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA.
+ */
+int lbm_record(lbm_ctx* ctx, int64_t nsteps, int64_t ckpt_every);
+
+/*
+ * lbm_backward - reverse sweep of the recorded rollout: the exact discrete
+ * adjoint of the stream-collide update (transposed collision Jacobian through
+ * f^eq, then reverse streaming), recomputing each segment of ckpt_every
+ * states from its checkpoint.
+ *   dL_drhoN [cells]: gradient of the loss with respect to the final density.
+ *   Outputs (any may be NULL): dL_drho0 [cells], dL_dU0 [D][cells],
+ *   dL_dT0 [cells] (lattice units), dL_domega (one double, host memory).
+ * Arrays are FP64 in `where` memory.  The adjoint runs in FP64 for LBM_FP64
+ * contexts and FP32 otherwise.  The recorded trajectory is kept (the call may
+ * be repeated with another dL_drhoN); the current state is restored to the
+ * final state of the rollout.
+ * Errors: LBM_ESTATE (nothing recorded), LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA.
+ */
+int lbm_backward(lbm_ctx* ctx, const double* dL_drhoN, double* dL_drho0, double* dL_dU0,
+                 double* dL_dT0, double* dL_domega, int where);
+
+/* lbm_release_record - free the checkpoints and segment buffers. */
+int lbm_release_record(lbm_ctx* ctx);
+
+/* lbm_synchronize - wait for all work on the context's stream. */
+int lbm_synchronize(lbm_ctx* ctx);
+
+/* lbm_launch_count - kernels this context has launched so far. */
+int64_t lbm_launch_count(const lbm_ctx* ctx);
+
+/* lbm_strerror - static text for an error code; lbm_last_error - detail of
+ * the last failure on the calling thread (empty string if none). */
+const char* lbm_strerror(int code);
+const char* lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_GB300_H */

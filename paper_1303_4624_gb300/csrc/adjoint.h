@@ -1,0 +1,65 @@
+// adjoint.h - host-side types shared by lbm_api.cu and adjoint.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <memory>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "common.h"
+
+namespace lbm {
+
+// One device allocation, made through the caller's allocator when one is set.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  lbm_free_fn free_fn = nullptr;
+  void* user = nullptr;
+  void* stream = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf();
+  void release();
+  int ensure(size_t nbytes, cudaStream_t st);
+};
+
+// A checkpointed rollout: S_0, S_k, S_2k, ... and the buffers of the reverse sweep.
+struct Record {
+  bool valid = false;
+  int64_t nsteps = 0;
+  int64_t k = 0;
+  int final_buf = 0;                            // state buffer holding S_N
+  std::vector<std::unique_ptr<DevBuf>> ckpt;    // ceil(nsteps / k) states
+  std::vector<std::unique_ptr<DevBuf>> seg;     // k - 1 replayed states
+  DevBuf nu[2];                                 // adjoint ping-pong, Q * cells of the adjoint type
+  DevBuf dldrho;                                // dL/drho_N staging (FP64)
+  DevBuf omega_acc;                             // per-block partial sums of dL/domega
+  DevBuf omega_out;                             // 1 double
+  DevBuf grads;                                 // host-output staging (D + 2) * cells FP64
+};
+
+struct CtxView {
+  int model, storage, D, Q;
+  const StorageOps* ops;
+  Grid g;
+  double omega;
+  cudaStream_t stream;
+  DevBuf* state[2];
+  int* cur;
+  DevBuf* fields;
+  bool inited;
+  int64_t* steps;
+  int64_t* launches;
+  Record* rec;
+};
+
+int ctx_fail(int code, const char* msg);
+int ctx_cuda_fail(cudaError_t e, const char* what);
+const ModelConst* ctx_model_const(int model);
+CtxView ctx_view(lbm_ctx* c);
+
+}  // namespace lbm

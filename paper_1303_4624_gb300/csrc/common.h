@@ -1,0 +1,74 @@
+// common.h - types shared by the host API and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+namespace lbm {
+
+constexpr int kMaxQc = 95;
+constexpr int kMaxGc = 10;
+
+// Per-model constants solved on the host (Formula 5) and kept in constant memory.
+struct ModelConst {
+  double W[kMaxGc];    // weight of each symmetry group
+  double X2[kMaxGc];   // |xi|^2 = a^2 |e|^2 of each group
+  float Wf[kMaxGc];
+  float X2f[kMaxGc];
+  double w[kMaxQc];    // weight per direction (storage order)
+  double a;            // sqrt(2) c: xi_i = a e_i
+  float af;
+  double c;
+  double T0;           // 1 / (2 c^2), lattice units
+};
+
+struct Grid {
+  int nx, ny, nz, nxy;
+  long long ncell;
+};
+
+// Launchers of one storage form (one translation unit each).  All enqueue on
+// `st` and return the launch status.
+struct StorageOps {
+  int elem_bytes;
+  cudaError_t (*upload)(const ModelConst* mc2);
+  cudaError_t (*init)(int model, const double* rho, const double* U, const double* T, void* dst,
+                      const Grid& g, cudaStream_t st);
+  cudaError_t (*step)(int model, const void* src, void* dst, const Grid& g, double omega,
+                      cudaStream_t st);
+  cudaError_t (*moments)(int model, const void* src, const Grid& g, double* rho, double* U,
+                         double* T, double* partials, cudaStream_t st);
+  cudaError_t (*get_f)(int model, const void* src, double* f, const Grid& g, cudaStream_t st);
+  cudaError_t (*set_f)(int model, const double* f, void* dst, const Grid& g, cudaStream_t st);
+  // Adjoint (lambda type: FP64 for the FP64 form, FP32 otherwise).
+  int adj_elem_bytes;
+  // One reverse step: nu_out = (collision Jacobian)^T lambda_{n+1} with
+  // lambda_{n+1}(x, i) = nu_next(x + e_i, i), or dL/drho_N(x) when dldrho != NULL;
+  // adds this step's dL/domega block partials into omega_acc[block].
+  cudaError_t (*adjoint_step)(int model, const void* state_n, const void* nu_next,
+                              const double* dldrho, void* nu_out, double* omega_acc,
+                              const Grid& g, double omega, cudaStream_t st);
+  // dL/d(rho0, U0, T0) from lambda_0(x, i) = nu0(x + e_i, i) and the initial fields.
+  cudaError_t (*grad_init)(int model, const void* nu0, const double* fields, double* d_rho,
+                           double* d_U, double* d_T, const Grid& g, cudaStream_t st);
+};
+
+// Blocks of the 3D cell launch shared by stream-collide and the adjoint step.
+inline int cell_block_x(int nx) { return nx >= 128 ? 128 : ((nx + 31) / 32) * 32; }
+inline long long cell_blocks(const Grid& g) {
+  const int bx = cell_block_x(g.nx);
+  return (long long)((g.nx + bx - 1) / bx) * g.ny * g.nz;
+}
+cudaError_t launch_sum_reduce(const double* partials, long long n, double* out, cudaStream_t st);
+
+extern const StorageOps kOpsFP64, kOpsFP32, kOpsFP16, kOpsBF16;
+
+constexpr int kAuditSlots = 8;
+constexpr int kMomentThreads = 256;
+inline int moment_blocks(long long ncell) {
+  return (int)((ncell + kMomentThreads - 1) / kMomentThreads);
+}
+cudaError_t launch_audit_reduce(const double* partials, int nblocks, double* out, cudaStream_t st);
+
+}  // namespace lbm

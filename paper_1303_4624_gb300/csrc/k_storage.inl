@@ -1,0 +1,116 @@
+// k_storage.inl - launchers of one storage form.  Included by k_fp64.cu,
+// k_fp32.cu, k_fp16.cu and k_bf16.cu after defining LBM_STORE (element type) and
+// LBM_OPS (name of the StorageOps table).
+#include "kernels.cuh"
+
+namespace lbm {
+namespace {
+
+using S = LBM_STORE;
+
+cudaError_t upload(const ModelConst* mc2) {
+  return cudaMemcpyToSymbol(c_mc, mc2, 2 * sizeof(ModelConst));
+}
+
+template <int M>
+cudaError_t init_m(const double* rho, const double* U, const double* T, void* dst, const Grid& g,
+                   cudaStream_t st) {
+  const int bs = 256;
+  const long long nb = (g.ncell + bs - 1) / bs;
+  k_init<M, S><<<(unsigned)nb, bs, 0, st>>>(rho, U, T, static_cast<S*>(dst), g);
+  return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t step_m(const void* src, void* dst, const Grid& g, double omega, cudaStream_t st) {
+  const int bx = cell_block_x(g.nx);
+  const dim3 grid((unsigned)((g.nx + bx - 1) / bx), (unsigned)g.ny, (unsigned)g.nz);
+  k_stream_collide<M, S><<<grid, bx, 0, st>>>(static_cast<const S*>(src), static_cast<S*>(dst), g,
+                                              omega);
+  return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t moments_m(const void* src, const Grid& g, double* rho, double* U, double* T,
+                      double* partials, cudaStream_t st) {
+  k_moments<M, S><<<moment_blocks(g.ncell), kMomentThreads, 0, st>>>(static_cast<const S*>(src),
+                                                                    g, rho, U, T, partials);
+  return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t get_f_m(const void* src, double* f, const Grid& g, cudaStream_t st) {
+  k_get_f<M, S><<<1024, 256, 0, st>>>(static_cast<const S*>(src), f, g);
+  return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t set_f_m(const double* f, void* dst, const Grid& g, cudaStream_t st) {
+  k_set_f<M, S><<<1024, 256, 0, st>>>(f, static_cast<S*>(dst), g);
+  return cudaGetLastError();
+}
+
+using L = std::conditional<std::is_same<S, double>::value, double, float>::type;
+
+template <int M>
+cudaError_t adjoint_m(const void* state_n, const void* nu_next, const double* dldrho, void* nu_out,
+                      double* omega_acc, const Grid& g, double omega, cudaStream_t st) {
+  const int bx = cell_block_x(g.nx);
+  const dim3 grid((unsigned)((g.nx + bx - 1) / bx), (unsigned)g.ny, (unsigned)g.nz);
+  if (dldrho)
+    k_adjoint<M, S, L, true><<<grid, bx, 0, st>>>(static_cast<const S*>(state_n), nullptr, dldrho,
+                                                 static_cast<L*>(nu_out), omega_acc, g, omega);
+  else
+    k_adjoint<M, S, L, false><<<grid, bx, 0, st>>>(static_cast<const S*>(state_n),
+                                                  static_cast<const L*>(nu_next), nullptr,
+                                                  static_cast<L*>(nu_out), omega_acc, g, omega);
+  return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t grad_init_m(const void* nu0, const double* fields, double* d_rho, double* d_U,
+                        double* d_T, const Grid& g, cudaStream_t st) {
+  const int bx = cell_block_x(g.nx);
+  const dim3 grid((unsigned)((g.nx + bx - 1) / bx), (unsigned)g.ny, (unsigned)g.nz);
+  k_grad_init<M, L><<<grid, bx, 0, st>>>(static_cast<const L*>(nu0), fields, d_rho, d_U, d_T, g);
+  return cudaGetLastError();
+}
+
+cudaError_t adjoint_step(int m, const void* state_n, const void* nu_next, const double* dldrho,
+                         void* nu_out, double* omega_acc, const Grid& g, double omega,
+                         cudaStream_t st) {
+  return m == 0 ? adjoint_m<0>(state_n, nu_next, dldrho, nu_out, omega_acc, g, omega, st)
+                : adjoint_m<1>(state_n, nu_next, dldrho, nu_out, omega_acc, g, omega, st);
+}
+cudaError_t grad_init(int m, const void* nu0, const double* fields, double* d_rho, double* d_U,
+                      double* d_T, const Grid& g, cudaStream_t st) {
+  return m == 0 ? grad_init_m<0>(nu0, fields, d_rho, d_U, d_T, g, st)
+                : grad_init_m<1>(nu0, fields, d_rho, d_U, d_T, g, st);
+}
+
+cudaError_t init(int m, const double* rho, const double* U, const double* T, void* dst,
+                 const Grid& g, cudaStream_t st) {
+  return m == 0 ? init_m<0>(rho, U, T, dst, g, st) : init_m<1>(rho, U, T, dst, g, st);
+}
+cudaError_t step(int m, const void* src, void* dst, const Grid& g, double omega, cudaStream_t st) {
+  return m == 0 ? step_m<0>(src, dst, g, omega, st) : step_m<1>(src, dst, g, omega, st);
+}
+cudaError_t moments(int m, const void* src, const Grid& g, double* rho, double* U, double* T,
+                    double* partials, cudaStream_t st) {
+  return m == 0 ? moments_m<0>(src, g, rho, U, T, partials, st)
+                : moments_m<1>(src, g, rho, U, T, partials, st);
+}
+cudaError_t get_f(int m, const void* src, double* f, const Grid& g, cudaStream_t st) {
+  return m == 0 ? get_f_m<0>(src, f, g, st) : get_f_m<1>(src, f, g, st);
+}
+cudaError_t set_f(int m, const double* f, void* dst, const Grid& g, cudaStream_t st) {
+  return m == 0 ? set_f_m<0>(f, dst, g, st) : set_f_m<1>(f, dst, g, st);
+}
+
+}  // namespace
+
+const StorageOps LBM_OPS = {(int)sizeof(S), upload, init,          step,
+                            moments,        get_f,  set_f,         (int)sizeof(L),
+                            adjoint_step,   grad_init};
+
+}  // namespace lbm

@@ -1,0 +1,668 @@
+// lbm_api.cu - host side of the C ABI declared in include/lbm.h.
+//
+// Holds the model tables (velocity sets expanded at compile time in
+// velset.cuh, weights solved here from Formula 5), the context object with its
+// ping-pong population buffers, argument validation and the launch sequences.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "common.h"
+#include "velset.cuh"
+#include "adjoint.h"
+
+using namespace lbm;
+
+// ================================================================ errors
+namespace {
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(LBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define LBM_CUDA(call)                                     \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);    \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+}  // namespace
+
+// ================================================================ model tables (Formula 5)
+namespace {
+
+// Printed weights (Tables 2 and 3) and c: the Newton start point.
+const double kStartD2Q33[8] = {0.161987, 0.143204, 0.0338840, 0.00556112,
+                               8.44799e-5, 0.00113254, 0.0128169, 3.45552e-6};
+const double kStartCD2Q33 = 0.819381;
+const double kStartD3Q95[10] = {0.206847, 0.00442257, 0.0333341, 0.0128902, 0.0287920,
+                                0.00264319, 0.000927908, 0.00106078, 0.000804376, 0.00274697};
+const double kStartCD3Q95 = 0.421803;
+
+struct HostModel {
+  VelSet vs;
+  double W[kMaxG];
+  double c;
+  double residual;
+  double w[kMaxQ];
+  ModelConst mc;
+};
+
+double dfact_odd(int n) {  // (n-1)!! for even n >= 0
+  double r = 1.0;
+  for (int k = n - 1; k > 1; k -= 2) r *= k;
+  return r;
+}
+
+// Normalised Gaussian moment prod_a (a-1)!!/2^(a/2): Formula 4 divided by pi^(D/2).
+double gauss_norm(const int a[3]) {
+  double r = 1.0;
+  for (int k = 0; k < 3; ++k) r *= dfact_odd(a[k]) / std::pow(2.0, a[k] / 2);
+  return r;
+}
+
+// Exponent classes of Formula 5 up to n_max = 8: doubled partitions of q <= 4
+// into at most D parts (Formula 8 counts them: 9 for D = 2, 11 for D = 3).
+void partitions_rec(int q, int maxpart, int parts_left, std::vector<int>& cur,
+                    std::vector<std::vector<int>>* out) {
+  if (q == 0) {
+    out->push_back(cur);
+    return;
+  }
+  if (parts_left == 0) return;
+  for (int p = (q < maxpart ? q : maxpart); p >= 1; --p) {
+    cur.push_back(p);
+    partitions_rec(q - p, p, parts_left - 1, cur, out);
+    cur.pop_back();
+  }
+}
+
+bool solve_dense(std::vector<double>& A, std::vector<double>& b, int n) {
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < n; ++r)
+      if (std::fabs(A[r * n + col]) > std::fabs(A[piv * n + col])) piv = r;
+    if (A[piv * n + col] == 0.0) return false;
+    if (piv != col) {
+      for (int k = 0; k < n; ++k) std::swap(A[col * n + k], A[piv * n + k]);
+      std::swap(b[col], b[piv]);
+    }
+    for (int r = col + 1; r < n; ++r) {
+      const double f = A[r * n + col] / A[col * n + col];
+      for (int k = col; k < n; ++k) A[r * n + k] -= f * A[col * n + k];
+      b[r] -= f * b[col];
+    }
+  }
+  for (int r = n - 1; r >= 0; --r) {
+    double s = b[r];
+    for (int k = r + 1; k < n; ++k) s -= A[r * n + k] * b[k];
+    b[r] = s / A[r * n + r];
+  }
+  return true;
+}
+
+bool build_host_model(int model, HostModel* hm) {
+  hm->vs = model == 0 ? make_velset<0>() : make_velset<1>();
+  const VelSet& vs = hm->vs;
+  const int G = vs.G, D = vs.D, n = G + 1;
+  // equations
+  std::vector<std::vector<int>> parts;
+  for (int q = 0; q <= 4; ++q) {
+    std::vector<int> cur;
+    partitions_rec(q, q, D, cur, &parts);
+  }
+  if ((int)parts.size() != n) return false;  // Formula 10: equations == unknowns
+  std::vector<double> Mg(parts.size() * G, 0.0), rhs(parts.size()), nn(parts.size());
+  for (size_t k = 0; k < parts.size(); ++k) {
+    int a[3] = {0, 0, 0};
+    for (size_t j = 0; j < parts[k].size(); ++j) a[j] = 2 * parts[k][j];
+    rhs[k] = gauss_norm(a);
+    nn[k] = a[0] + a[1] + a[2];
+    for (int i = 0; i < vs.Q; ++i) {
+      double p = 1.0;
+      for (int d = 0; d < 3; ++d)
+        for (int r = 0; r < a[d]; ++r) p *= vs.e[i][d];
+      Mg[k * G + vs.grp[i]] += p;
+    }
+  }
+  std::vector<double> x(n);
+  for (int g = 0; g < G; ++g) x[g] = model == 0 ? kStartD2Q33[g] : kStartD3Q95[g];
+  x[G] = model == 0 ? kStartCD2Q33 : kStartCD3Q95;
+  auto residual = [&](const std::vector<double>& xv, std::vector<double>* F) {
+    double mx = 0;
+    for (int k = 0; k < n; ++k) {
+      double s = 0;
+      for (int g = 0; g < G; ++g) s += Mg[k * G + g] * xv[g];
+      (*F)[k] = s * std::pow(xv[G], nn[k]) - rhs[k];
+      mx = std::fmax(mx, std::fabs((*F)[k]));
+    }
+    return mx;
+  };
+  std::vector<double> F(n), J(n * n);
+  for (int it = 0; it < 60; ++it) {
+    residual(x, &F);
+    for (int k = 0; k < n; ++k) {
+      double s = 0;
+      for (int g = 0; g < G; ++g) {
+        J[k * n + g] = Mg[k * G + g] * std::pow(x[G], nn[k]);
+        s += Mg[k * G + g] * x[g];
+      }
+      J[k * n + G] = nn[k] > 0 ? s * nn[k] * std::pow(x[G], nn[k] - 1) : 0.0;
+    }
+    std::vector<double> dx(n);
+    for (int k = 0; k < n; ++k) dx[k] = -F[k];
+    if (!solve_dense(J, dx, n)) return false;
+    double step = 0;
+    for (int k = 0; k < n; ++k) {
+      x[k] += dx[k];
+      step = std::fmax(step, std::fabs(dx[k]));
+    }
+    if (step < 1e-17) break;
+  }
+  hm->residual = residual(x, &F);
+  for (int g = 0; g < G; ++g) hm->W[g] = x[g];
+  hm->c = x[G];
+  for (int i = 0; i < vs.Q; ++i) hm->w[i] = hm->W[vs.grp[i]];
+
+  ModelConst& mc = hm->mc;
+  std::memset(&mc, 0, sizeof mc);
+  const double a = std::sqrt(2.0) * hm->c;
+  for (int g = 0; g < G; ++g) {
+    mc.W[g] = hm->W[g];
+    mc.X2[g] = a * a * vs.e2[g];
+    mc.Wf[g] = (float)mc.W[g];
+    mc.X2f[g] = (float)mc.X2[g];
+  }
+  for (int i = 0; i < vs.Q; ++i) mc.w[i] = hm->w[i];
+  mc.a = a;
+  mc.af = (float)a;
+  mc.c = hm->c;
+  mc.T0 = 1.0 / (2.0 * hm->c * hm->c);
+  return hm->residual < 1e-13;
+}
+
+std::mutex g_model_mu;
+HostModel g_models[2];
+bool g_model_ok[2] = {false, false};
+std::vector<int> g_uploaded;  // devices whose constant tables are current
+
+const HostModel* host_model(int model) {
+  std::lock_guard<std::mutex> lk(g_model_mu);
+  if (!g_model_ok[model]) {
+    if (!build_host_model(model, &g_models[model])) return nullptr;
+    g_model_ok[model] = true;
+  }
+  return &g_models[model];
+}
+
+const StorageOps* ops_for(int storage) {
+  switch (storage) {
+    case LBM_FP64: return &kOpsFP64;
+    case LBM_FP32: return &kOpsFP32;
+    case LBM_FP16DEV: return &kOpsFP16;
+    case LBM_BF16DEV: return &kOpsBF16;
+    default: return nullptr;
+  }
+}
+
+int ensure_uploaded(int dev) {
+  const HostModel* m0 = host_model(0);
+  const HostModel* m1 = host_model(1);
+  if (!m0 || !m1) return fail(LBM_EINVAL, "model table solve failed");
+  std::lock_guard<std::mutex> lk(g_model_mu);
+  for (int d : g_uploaded)
+    if (d == dev) return LBM_OK;
+  ModelConst both[2] = {m0->mc, m1->mc};
+  const StorageOps* all[4] = {&kOpsFP64, &kOpsFP32, &kOpsFP16, &kOpsBF16};
+  for (auto* o : all) {
+    cudaError_t e = o->upload(both);
+    if (e != cudaSuccess) return cuda_fail(e, "constant table upload");
+  }
+  g_uploaded.push_back(dev);
+  return LBM_OK;
+}
+
+// ================================================================ allocation
+std::mutex g_alloc_mu;
+lbm_alloc_fn g_alloc = nullptr;
+lbm_free_fn g_free = nullptr;
+void* g_alloc_user = nullptr;
+
+}  // namespace
+
+namespace lbm {
+
+DevBuf::~DevBuf() { release(); }
+
+void DevBuf::release() {
+  if (!p) return;
+  if (free_fn) free_fn(p, stream, user);
+  else cudaFree(p);
+  p = nullptr;
+  bytes = 0;
+}
+
+int DevBuf::ensure(size_t nbytes, cudaStream_t st) {
+  if (p && bytes >= nbytes) return LBM_OK;
+  release();
+  if (nbytes == 0) return LBM_OK;
+  lbm_alloc_fn a;
+  lbm_free_fn f;
+  void* u;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    a = g_alloc;
+    f = g_free;
+    u = g_alloc_user;
+  }
+  if (a) {
+    p = a(nbytes, (void*)st, u);
+    if (!p) return fail(LBM_ENOMEM, "allocator returned NULL for %zu bytes", nbytes);
+    free_fn = f;
+    user = u;
+    stream = (void*)st;
+  } else {
+    cudaError_t e = cudaMalloc(&p, nbytes);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      cudaGetLastError();
+      return fail(LBM_ENOMEM, "cudaMalloc(%zu): %s", nbytes, cudaGetErrorString(e));
+    }
+    free_fn = nullptr;
+  }
+  bytes = nbytes;
+  return LBM_OK;
+}
+
+}  // namespace lbm
+
+// ================================================================ context
+struct lbm_ctx {
+  int model = 0, storage = 0, dev = 0, D = 0, Q = 0;
+  const StorageOps* ops = nullptr;
+  Grid g{};
+  double omega = 1.0;
+  cudaStream_t stream = nullptr;
+  DevBuf state[2];
+  int cur = 0;
+  DevBuf fields;      // initial rho | U (D) | T, FP64
+  DevBuf mom;         // host-output staging for moments / populations
+  DevBuf partials;    // audit block partials
+  DevBuf audit_out;   // 8 doubles
+  bool inited = false;
+  int64_t steps = 0;
+  int64_t launches = 0;
+  Record rec;         // checkpointed rollout (adjoint.h)
+};
+
+namespace {
+
+size_t state_bytes(const lbm_ctx* c) {
+  return (size_t)c->Q * (size_t)c->g.ncell * (size_t)c->ops->elem_bytes;
+}
+
+bool all_finite(const double* p, size_t n) {
+  for (size_t k = 0; k < n; ++k)
+    if (!std::isfinite(p[k])) return false;
+  return true;
+}
+
+int do_steps(lbm_ctx* c, int64_t n) {
+  for (int64_t k = 0; k < n; ++k) {
+    cudaError_t e = c->ops->step(c->model, c->state[c->cur].p, c->state[c->cur ^ 1].p, c->g,
+                                 c->omega, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "stream_collide launch");
+    c->cur ^= 1;
+    c->launches += 1;
+  }
+  c->steps += n;
+  return LBM_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- internal hooks for adjoint.cu
+namespace lbm {
+int ctx_fail(int code, const char* msg) { return fail(code, "%s", msg); }
+int ctx_cuda_fail(cudaError_t e, const char* what) { return cuda_fail(e, what); }
+const ModelConst* ctx_model_const(int model) {
+  const HostModel* m = host_model(model);
+  return m ? &m->mc : nullptr;
+}
+CtxView ctx_view(lbm_ctx* c) {
+  CtxView v;
+  v.model = c->model;
+  v.storage = c->storage;
+  v.D = c->D;
+  v.Q = c->Q;
+  v.ops = c->ops;
+  v.g = c->g;
+  v.omega = c->omega;
+  v.stream = c->stream;
+  v.state[0] = &c->state[0];
+  v.state[1] = &c->state[1];
+  v.cur = &c->cur;
+  v.fields = &c->fields;
+  v.inited = c->inited;
+  v.steps = &c->steps;
+  v.launches = &c->launches;
+  v.rec = &c->rec;
+  return v;
+}
+}  // namespace lbm
+
+// ================================================================ C ABI
+extern "C" {
+
+const char* lbm_strerror(int code) {
+  switch (code) {
+    case LBM_OK: return "ok";
+    case LBM_EINVAL: return "invalid argument";
+    case LBM_ENOMEM: return "out of device memory";
+    case LBM_ECUDA: return "CUDA error";
+    case LBM_EUNSTABLE: return "non-finite populations";
+    case LBM_ESTATE: return "call out of order";
+    default: return "unknown error";
+  }
+}
+
+const char* lbm_last_error(void) { return g_last_error.c_str(); }
+
+int lbm_model_info(int model, int* Q, int* D, int* reach, int32_t* e, double* w, double* c,
+                   double* T0) {
+  if (model != LBM_D2Q33 && model != LBM_D3Q95) return fail(LBM_EINVAL, "unknown model %d", model);
+  const HostModel* hm = host_model(model);
+  if (!hm) return fail(LBM_EINVAL, "model table solve failed");
+  const VelSet& vs = hm->vs;
+  if (Q) *Q = vs.Q;
+  if (D) *D = vs.D;
+  if (reach) *reach = vs.R;
+  if (e)
+    for (int i = 0; i < vs.Q; ++i)
+      for (int d = 0; d < vs.D; ++d) e[i * vs.D + d] = vs.e[i][d];
+  if (w)
+    for (int i = 0; i < vs.Q; ++i) w[i] = hm->w[i];
+  if (c) *c = hm->c;
+  if (T0) *T0 = hm->mc.T0;
+  return LBM_OK;
+}
+
+int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn free_fn, void* user) {
+  if ((alloc == nullptr) != (free_fn == nullptr))
+    return fail(LBM_EINVAL, "allocator and free function must both be set or both be NULL");
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc = alloc;
+  g_free = free_fn;
+  g_alloc_user = user;
+  return LBM_OK;
+}
+
+int lbm_create(lbm_ctx** out, int model, const int64_t dims[3], double omega, int storage,
+               void* stream) {
+  if (!out) return fail(LBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (model != LBM_D2Q33 && model != LBM_D3Q95) return fail(LBM_EINVAL, "unknown model %d", model);
+  const StorageOps* ops = ops_for(storage);
+  if (!ops) return fail(LBM_EINVAL, "unknown storage %d", storage);
+  if (!dims) return fail(LBM_EINVAL, "dims is NULL");
+  for (int k = 0; k < 3; ++k)
+    if (dims[k] < 1 || dims[k] > (int64_t)1 << 30) return fail(LBM_EINVAL, "dims[%d] = %lld", k, (long long)dims[k]);
+  if (model == LBM_D2Q33 && dims[2] != 1) return fail(LBM_EINVAL, "D2Q33 needs Nz == 1");
+  const int64_t ncell = dims[0] * dims[1] * dims[2];
+  if (ncell >= ((int64_t)1 << 31)) return fail(LBM_EINVAL, "too many cells (%lld)", (long long)ncell);
+  if (dims[1] > 65535 || dims[2] > 65535) return fail(LBM_EINVAL, "Ny and Nz must be <= 65535");
+  if (!(omega >= 0.0 && omega < 2.0)) return fail(LBM_EINVAL, "omega = %g outside [0, 2)", omega);
+  const HostModel* hm = host_model(model);
+  if (!hm) return fail(LBM_EINVAL, "model table solve failed");
+
+  int dev = 0;
+  LBM_CUDA(cudaGetDevice(&dev));
+  int rc = ensure_uploaded(dev);
+  if (rc) return rc;
+
+  lbm_ctx* c = new lbm_ctx();
+  c->model = model;
+  c->storage = storage;
+  c->dev = dev;
+  c->D = hm->vs.D;
+  c->Q = hm->vs.Q;
+  c->ops = ops;
+  c->g.nx = (int)dims[0];
+  c->g.ny = (int)dims[1];
+  c->g.nz = (int)dims[2];
+  c->g.nxy = (int)(dims[0] * dims[1]);
+  c->g.ncell = ncell;
+  c->omega = omega;
+  c->stream = (cudaStream_t)stream;
+  const size_t sb = state_bytes(c);
+  if ((rc = c->state[0].ensure(sb, c->stream)) || (rc = c->state[1].ensure(sb, c->stream)) ||
+      (rc = c->partials.ensure((size_t)moment_blocks(ncell) * kAuditSlots * sizeof(double),
+                               c->stream)) ||
+      (rc = c->audit_out.ensure(kAuditSlots * sizeof(double), c->stream))) {
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return LBM_OK;
+}
+
+int lbm_destroy(lbm_ctx* c) {
+  if (!c) return LBM_OK;
+  DeviceGuard dg(c->dev);
+  cudaStreamSynchronize(c->stream);
+  delete c;
+  return LBM_OK;
+}
+
+int lbm_set_omega(lbm_ctx* c, double omega) {
+  if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+  if (!(omega >= 0.0 && omega < 2.0)) return fail(LBM_EINVAL, "omega = %g outside [0, 2)", omega);
+  c->omega = omega;
+  c->rec.valid = false;
+  return LBM_OK;
+}
+
+int lbm_set_stream(lbm_ctx* c, void* stream) {
+  if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+  c->stream = (cudaStream_t)stream;
+  return LBM_OK;
+}
+
+int lbm_init(lbm_ctx* c, const double* rho, const double* U, const double* T, int where) {
+  if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+  if (!rho || !U || !T) return fail(LBM_EINVAL, "rho, U and T are required");
+  if (where != LBM_HOST && where != LBM_DEVICE) return fail(LBM_EINVAL, "bad where");
+  const size_t n = (size_t)c->g.ncell;
+  if (where == LBM_HOST) {
+    for (size_t k = 0; k < n; ++k)
+      if (!(std::isfinite(rho[k]) && rho[k] > 0.0)) return fail(LBM_EINVAL, "rho[%zu] = %g", k, rho[k]);
+    for (size_t k = 0; k < n; ++k)
+      if (!(std::isfinite(T[k]) && T[k] > 0.0)) return fail(LBM_EINVAL, "T[%zu] = %g", k, T[k]);
+    if (!all_finite(U, n * c->D)) return fail(LBM_EINVAL, "U has non-finite values");
+  }
+  DeviceGuard dg(c->dev);
+  int rc = c->fields.ensure((size_t)(c->D + 2) * n * sizeof(double), c->stream);
+  if (rc) return rc;
+  double* f = static_cast<double*>(c->fields.p);
+  const cudaMemcpyKind kind = where == LBM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  LBM_CUDA(cudaMemcpyAsync(f, rho, n * sizeof(double), kind, c->stream));
+  LBM_CUDA(cudaMemcpyAsync(f + n, U, (size_t)c->D * n * sizeof(double), kind, c->stream));
+  LBM_CUDA(cudaMemcpyAsync(f + (size_t)(c->D + 1) * n, T, n * sizeof(double), kind, c->stream));
+  c->cur = 0;
+  cudaError_t e = c->ops->init(c->model, f, f + n, f + (size_t)(c->D + 1) * n, c->state[0].p, c->g,
+                               c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "init launch");
+  c->launches += 1;
+  c->inited = true;
+  c->steps = 0;
+  c->rec.valid = false;
+  return LBM_OK;
+}
+
+int lbm_step(lbm_ctx* c, int64_t n) {
+  if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+  if (!c->inited) return fail(LBM_ESTATE, "lbm_step before lbm_init");
+  if (n < 0) return fail(LBM_EINVAL, "n = %lld", (long long)n);
+  DeviceGuard dg(c->dev);
+  return do_steps(c, n);
+}
+
+int64_t lbm_steps_done(const lbm_ctx* c) { return c ? c->steps : -1; }
+int64_t lbm_launch_count(const lbm_ctx* c) { return c ? c->launches : -1; }
+
+int lbm_moments(lbm_ctx* c, double* rho, double* U, double* T, int where) {
+  if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+  if (!c->inited) return fail(LBM_ESTATE, "lbm_moments before lbm_init");
+  if (where != LBM_HOST && where != LBM_DEVICE) return fail(LBM_EINVAL, "bad where");
+  DeviceGuard dg(c->dev);
+  const size_t n = (size_t)c->g.ncell;
+  double *dr = rho, *du = U, *dt = T;
+  if (where == LBM_HOST) {
+    int rc = c->mom.ensure((size_t)(c->D + 2) * n * sizeof(double), c->stream);
+    if (rc) return rc;
+    double* m = static_cast<double*>(c->mom.p);
+    dr = rho ? m : nullptr;
+    du = U ? m + n : nullptr;
+    dt = T ? m + (size_t)(c->D + 1) * n : nullptr;
+  }
+  cudaError_t e = c->ops->moments(c->model, c->state[c->cur].p, c->g, dr, du, dt,
+                                  static_cast<double*>(c->partials.p), c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "moments launch");
+  c->launches += 1;
+  if (where == LBM_HOST) {
+    if (rho) LBM_CUDA(cudaMemcpyAsync(rho, dr, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (U) LBM_CUDA(cudaMemcpyAsync(U, du, (size_t)c->D * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (T) LBM_CUDA(cudaMemcpyAsync(T, dt, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+  }
+  return LBM_OK;
+}
+
+int lbm_audit(lbm_ctx* c, double out[8]) {
+  if (!c || !out) return fail(LBM_EINVAL, "ctx or out is NULL");
+  if (!c->inited) return fail(LBM_ESTATE, "lbm_audit before lbm_init");
+  DeviceGuard dg(c->dev);
+  cudaError_t e = c->ops->moments(c->model, c->state[c->cur].p, c->g, nullptr, nullptr, nullptr,
+                                  static_cast<double*>(c->partials.p), c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "audit launch");
+  e = launch_audit_reduce(static_cast<double*>(c->partials.p), moment_blocks(c->g.ncell),
+                          static_cast<double*>(c->audit_out.p), c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "audit reduce launch");
+  c->launches += 2;
+  LBM_CUDA(cudaMemcpyAsync(out, c->audit_out.p, kAuditSlots * sizeof(double),
+                           cudaMemcpyDeviceToHost, c->stream));
+  LBM_CUDA(cudaStreamSynchronize(c->stream));
+  return out[6] > 0 ? fail(LBM_EUNSTABLE, "%g non-finite populations", out[6]) : LBM_OK;
+}
+
+int lbm_get_populations(lbm_ctx* c, double* f, int where) {
+  if (!c || !f) return fail(LBM_EINVAL, "ctx or f is NULL");
+  if (!c->inited) return fail(LBM_ESTATE, "no state yet");
+  if (where != LBM_HOST && where != LBM_DEVICE) return fail(LBM_EINVAL, "bad where");
+  DeviceGuard dg(c->dev);
+  const size_t n = (size_t)c->Q * (size_t)c->g.ncell;
+  double* dst = f;
+  if (where == LBM_HOST) {
+    int rc = c->mom.ensure(n * sizeof(double), c->stream);
+    if (rc) return rc;
+    dst = static_cast<double*>(c->mom.p);
+  }
+  cudaError_t e = c->ops->get_f(c->model, c->state[c->cur].p, dst, c->g, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "get_f launch");
+  c->launches += 1;
+  if (where == LBM_HOST) {
+    LBM_CUDA(cudaMemcpyAsync(f, dst, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+  }
+  return LBM_OK;
+}
+
+int lbm_set_populations(lbm_ctx* c, const double* f, int where) {
+  if (!c || !f) return fail(LBM_EINVAL, "ctx or f is NULL");
+  if (where != LBM_HOST && where != LBM_DEVICE) return fail(LBM_EINVAL, "bad where");
+  DeviceGuard dg(c->dev);
+  const size_t n = (size_t)c->Q * (size_t)c->g.ncell;
+  const double* srcp = f;
+  if (where == LBM_HOST) {
+    if (!all_finite(f, n)) return fail(LBM_EINVAL, "populations have non-finite values");
+    int rc = c->mom.ensure(n * sizeof(double), c->stream);
+    if (rc) return rc;
+    LBM_CUDA(cudaMemcpyAsync(c->mom.p, f, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    srcp = static_cast<const double*>(c->mom.p);
+  }
+  c->cur = 0;
+  cudaError_t e = c->ops->set_f(c->model, srcp, c->state[0].p, c->g, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "set_f launch");
+  c->launches += 1;
+  if (where == LBM_HOST) LBM_CUDA(cudaStreamSynchronize(c->stream));
+  c->inited = true;
+  c->steps = 0;
+  c->rec.valid = false;
+  return LBM_OK;
+}
+
+int lbm_get_raw(lbm_ctx* c, void* h, size_t bytes, int where) {
+  if (!c || !h) return fail(LBM_EINVAL, "ctx or h is NULL");
+  if (!c->inited) return fail(LBM_ESTATE, "no state yet");
+  if (bytes != state_bytes(c)) return fail(LBM_EINVAL, "bytes = %zu, state is %zu", bytes, state_bytes(c));
+  if (where != LBM_HOST && where != LBM_DEVICE) return fail(LBM_EINVAL, "bad where");
+  DeviceGuard dg(c->dev);
+  LBM_CUDA(cudaMemcpyAsync(h, c->state[c->cur].p, bytes,
+                           where == LBM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                           c->stream));
+  if (where == LBM_HOST) LBM_CUDA(cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+int lbm_set_raw(lbm_ctx* c, const void* h, size_t bytes, int where) {
+  if (!c || !h) return fail(LBM_EINVAL, "ctx or h is NULL");
+  if (bytes != state_bytes(c)) return fail(LBM_EINVAL, "bytes = %zu, state is %zu", bytes, state_bytes(c));
+  if (where != LBM_HOST && where != LBM_DEVICE) return fail(LBM_EINVAL, "bad where");
+  DeviceGuard dg(c->dev);
+  c->cur = 0;
+  LBM_CUDA(cudaMemcpyAsync(c->state[0].p, h, bytes,
+                           where == LBM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                           c->stream));
+  if (where == LBM_HOST) LBM_CUDA(cudaStreamSynchronize(c->stream));
+  c->inited = true;
+  c->steps = 0;
+  c->rec.valid = false;
+  return LBM_OK;
+}
+
+int lbm_synchronize(lbm_ctx* c) {
+  if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+  DeviceGuard dg(c->dev);
+  LBM_CUDA(cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+}  // extern "C"

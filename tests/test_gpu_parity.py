@@ -1,0 +1,201 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (the benchmark spec): FP64 form 1e-12 relative, FP32 form 1e-5 relative,
+streaming indices bit-exact.  Populations are compared as the deviation
+h_i = f_i / w_i - 1, i.e. relative to the rest-state population w_i, because
+individual f_i of the outer shells can pass through zero; rho and T relative,
+U relative to the sound-speed scale sqrt(T0).
+"""
+import numpy as np
+import pytest
+
+from oracle import lbm as olbm
+from oracle.model import get_model
+from paper_1303_4624_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+
+
+def run_both(lbm, model, storage, fields, omega, steps, dims):
+    mdl = get_model(model)
+    T = fields.theta * mdl.T0
+    S = olbm.init_populations(mdl, fields.rho, fields.U, T)
+    S = olbm.run(mdl, S, omega, steps)
+    lat = lbm.Lattice(model, dims, omega, storage)
+    info = lat.info
+    lat.init(fields.rho, fields.U, fields.theta * info["T0"])
+    lat.step(steps)
+    return mdl, S, lat
+
+
+def to_oracle_order(mdl, lat, f):
+    """Reorder GPU populations [Q, ...] (library direction order) to the oracle's order."""
+    pos = {tuple(v): j for j, v in enumerate(lat.info["e"].tolist())}
+    perm = [pos[tuple(v)] for v in mdl.e.tolist()]
+    return f[perm]
+
+
+def compare(mdl, S, lat, tol):
+    f = to_oracle_order(mdl, lat, lat.populations())
+    dh = np.abs(f - S) / mdl.w.reshape((-1, 1, 1, 1))
+    rho, U, T = lat.moments()
+    r0, U0, T0 = olbm.macroscopic(mdl, S)
+    err = {
+        "h": float(dh.max()),
+        "rho": float(np.max(np.abs(rho - r0) / r0)),
+        "T": float(np.max(np.abs(T - T0) / T0)),
+        "U": float(np.max(np.abs(U - U0)) / np.sqrt(mdl.T0)),
+    }
+    assert max(err.values()) <= tol, err
+    return err
+
+
+def test_d2q33_fp64_riemann_256x8_200_steps(lbm):
+    """The D2Q33 FP64 workload in full: 256 x 8, 200 steps, omega 1.5."""
+    wl, fields = W.d2q33_riemann()
+    mdl, S, lat = run_both(lbm, "D2Q33", "fp64", fields, wl.omega, wl.steps, wl.dims)
+    compare(mdl, S, lat, TOL["fp64"])
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+def test_d3q95_riemann_ragged_grid(lbm, storage):
+    """165 x 6 x 5: two x tiles of 128 threads plus a ragged tail, y/z smaller than the reach."""
+    dims = (165, 6, 5)
+    fields = W.riemann_planar(3, *dims, 82, (1.0, 1.0), (0.6, 0.75), seed=3)
+    steps = 12 if storage == "fp64" else 40
+    mdl, S, lat = run_both(lbm, "D3Q95", storage, fields, 1.6, steps, dims)
+    compare(mdl, S, lat, TOL[storage])
+
+
+@pytest.mark.parametrize("model,dims", [("D3Q95", (3, 2, 4)), ("D3Q95", (1, 1, 1)),
+                                        ("D2Q33", (3, 2, 1)), ("D2Q33", (33, 1, 1))])
+def test_grids_smaller_than_the_reach(lbm, model, dims):
+    rng = np.random.default_rng(4)
+    mdl = get_model(model)
+    shape = dims[::-1]
+    rho = 1.0 + 0.05 * rng.standard_normal(shape)
+    U = 0.05 * rng.standard_normal((mdl.D,) + shape)
+    theta = 1.0 + 0.05 * rng.standard_normal(shape)
+    fields = W.Fields(rho, U, theta)
+    mdl, S, lat = run_both(lbm, model, "fp64", fields, 1.3, 7, dims)
+    compare(mdl, S, lat, TOL["fp64"])
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("model", ["D2Q33", "D3Q95"])
+def test_init_is_the_discrete_equilibrium(lbm, model, storage):
+    mdl = get_model(model)
+    dims = (40, 3, 2) if model == "D3Q95" else (40, 3, 1)
+    rng = np.random.default_rng(5)
+    shape = dims[::-1]
+    rho = 1.0 + 0.2 * rng.uniform(-1, 1, shape)
+    U = 0.1 * rng.uniform(-1, 1, (mdl.D,) + shape)
+    theta = 1.0 + 0.2 * rng.uniform(-1, 1, shape)
+    lat = lbm.Lattice(model, dims, 1.0, storage)
+    lat.init(rho, U, theta * lat.info["T0"])
+    S = olbm.init_populations(mdl, rho, U, theta * mdl.T0)
+    wv = mdl.w.reshape((-1, 1, 1, 1))
+    h_ref = S / wv - 1.0
+    dh = np.abs(to_oracle_order(mdl, lat, lat.populations()) - S) / wv
+    # one round-to-nearest of h = f/w - 1 in the storage type: half an ulp, relative
+    u = {"fp64": 2.0 ** -52, "fp32": 2.0 ** -24, "fp16": 2.0 ** -11, "bf16": 2.0 ** -8}[storage]
+    assert np.all(dh <= u * np.abs(h_ref) * (1 + 1e-6) + 1e-13)
+
+
+def label_array(Q, shape, storage):
+    """Integer labels exactly representable in the storage type."""
+    n = int(np.prod(shape))
+    cell = np.arange(n).reshape(shape)
+    mod = {"fp64": 1 << 40, "fp32": 1 << 23, "fp16": 2039, "bf16": 251}[storage]
+    lab = np.stack([(cell * 3 + 7 * i) % mod + 1 for i in range(Q)]).astype(np.float64)
+    return lab
+
+
+def as_storage(a, storage):
+    if storage == "fp64":
+        return a.astype(np.float64)
+    if storage == "fp32":
+        return a.astype(np.float32)
+    if storage == "fp16":
+        return a.astype(np.float16)
+    # bf16: the top 16 bits of the FP32 pattern (exact for these small integers)
+    return (a.astype(np.float32).view(np.uint32) >> 16).astype(np.uint16)
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("model,dims", [("D3Q95", (37, 6, 7)), ("D3Q95", (2, 3, 4)),
+                                        ("D2Q33", (131, 5, 1)), ("D2Q33", (3, 2, 1))])
+def test_streaming_is_a_bit_exact_permutation(lbm, model, dims, storage):
+    """omega = 0: after n steps h_i(x) = h_i((x - n e_i) mod N) bit for bit."""
+    lat = lbm.Lattice(model, dims, 0.0, storage)
+    Q = lat.info["Q"]
+    e = lat.info["e"]
+    shape = dims[::-1]
+    lab = as_storage(label_array(Q, shape, storage), storage)
+    lat.set_raw(lab)
+    n = 3
+    lat.step(n)
+    got = lat.raw()
+    nz, ny, nx = shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    for i in range(Q):
+        ex, ey = int(e[i, 0]), int(e[i, 1])
+        ez = int(e[i, 2]) if e.shape[1] == 3 else 0
+        src = (((z - n * ez) % nz) * ny + (y - n * ey) % ny) * nx + (x - n * ex) % nx
+        expect = lab[i].reshape(-1)[src]
+        assert np.array_equal(got[i].view(np.uint8), expect.view(np.uint8)), i
+
+
+def test_d3q95_fp32_full_size_128x64x64(lbm):
+    """The D3Q95 FP32 workload at full size (128 x 64 x 64, omega 1.6) in the launch
+    configuration the benchmark times: every population after 2 steps against the
+    oracle, plus the FP64 conservation audit after 200 steps."""
+    wl, fields = W.d3q95_riemann()
+    mdl, S, lat = run_both(lbm, "D3Q95", "fp32", fields, wl.omega, 2, wl.dims)
+    compare(mdl, S, lat, TOL["fp32"])
+    a0 = olbm.audit(mdl, olbm.init_populations(mdl, fields.rho, fields.U, fields.theta * mdl.T0))
+    lat.step(198)
+    a1 = lat.audit()
+    assert a1["nonfinite"] == 0 and a1["cells"] == wl.cells
+    assert abs(a1["mass"] / a0["mass"] - 1) < 1e-5
+    assert abs(a1["energy"] / a0["energy"] - 1) < 1e-5
+    assert np.max(np.abs(a1["momentum"])) / a0["mass"] < 1e-6
+
+
+def test_audit_matches_oracle(lbm):
+    dims = (24, 5, 4)
+    fields = W.riemann_planar(3, *dims, 12, (1.0, 1.0), (0.6, 0.75), seed=8)
+    mdl, S, lat = run_both(lbm, "D3Q95", "fp64", fields, 1.6, 5, dims)
+    a = lat.audit()
+    o = olbm.audit(mdl, S)
+    assert abs(a["mass"] - o["mass"]) < 1e-12 * o["mass"]
+    assert abs(a["energy"] - o["energy"]) < 1e-12 * o["energy"]
+    assert np.max(np.abs(a["momentum"] - o["momentum"])) < 1e-12 * o["mass"]
+    assert abs(a["min_f_over_w"] - o["min_f_over_w"]) < 1e-12
+    assert a["nonfinite"] == 0
+
+
+def test_errors_are_reported_before_launch(lbm):
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.Lattice("D3Q95", (8, 8, 8), 2.5, "fp32")
+    assert ei.value.code == lbm.LBM_EINVAL
+    lat = lbm.Lattice("D3Q95", (8, 8, 8), 1.0, "fp32")
+    with pytest.raises(lbm.LbmError) as ei:
+        lat.step(1)
+    assert ei.value.code == lbm.LBM_ESTATE
+    with pytest.raises(lbm.LbmError) as ei:
+        lat.set_raw(np.zeros(10, dtype=np.float32))
+    assert ei.value.code == lbm.LBM_EINVAL
+    rho = np.ones((8, 8, 8))
+    with pytest.raises(lbm.LbmError) as ei:
+        lat.init(-rho, np.zeros((3, 8, 8, 8)), rho)
+    assert ei.value.code == lbm.LBM_EINVAL
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_backward(lat.ctx, rho)
+    assert ei.value.code == lbm.LBM_ESTATE
+    n0 = lbm.lbm_launch_count(lat.ctx)
+    lat.init(rho, np.zeros((3, 8, 8, 8)), rho * lat.info["T0"])
+    lat.step(4)
+    assert lbm.lbm_launch_count(lat.ctx) == n0 + 5
