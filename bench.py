@@ -360,7 +360,8 @@ from paper_1303_4624_gb300 import workloads as W
 mdl = get_model("D3Q95")
 wl, f = W.d3q95_riemann(nx=128, ny=%d, nz=%d)
 S = lbm.init_populations(mdl, f.rho, f.U, f.theta * mdl.T0)
-S = lbm.step(mdl, S, wl.omega)
+for _ in range(max(1, %d)):
+    S = lbm.step(mdl, S, wl.omega)
 n = 0
 t0 = time.perf_counter()
 while True:
@@ -373,12 +374,12 @@ print(json.dumps({"steps": n, "seconds": dt, "cells": wl.cells}))
 """
 
 
-def run_oracle_sample(ny, nz, max_steps, budget_s):
+def run_oracle_sample(ny, nz, max_steps, budget_s, warmup=1):
     env = dict(os.environ)
     cores = os.cpu_count() or 1
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = str(cores)
-    code = CPU_SAMPLE % (ROOT, ny, nz, max_steps, budget_s)
+    code = CPU_SAMPLE % (ROOT, ny, nz, warmup, max_steps, budget_s)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
                        timeout=budget_s * 4 + 120)
     if r.returncode != 0:
@@ -406,7 +407,7 @@ def run_reference(args):
     budget = 120.0
     cells = max(128, min(128 * 64 * 64, int(budget / (total * 1.2e-5))))
     ny = nz = max(1, int(math.sqrt(cells / 128)))
-    res = run_oracle_sample(ny, nz, total, budget * 1.5)
+    res = run_oracle_sample(ny, nz, args.steps, budget * 1.5, warmup=args.warmup)
     value = res["cells"] * res["steps"] / res["seconds"] / 1e6
     line = {
         "impl": "reference",
@@ -415,7 +416,7 @@ def run_reference(args):
         "unit": "MLUPS",
         "n_gpus": world,
         "steps": res["steps"],
-        "warmup": 0,
+        "warmup": args.warmup,
         "ms_per_step": round(res["seconds"] / res["steps"] * 1e3, 3),
         "higher_is_better": True,
         "scaling": "weak",

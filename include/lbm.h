@@ -48,6 +48,7 @@ extern "C" {
 #define LBM_ECUDA     -3   /* a CUDA runtime call or kernel launch failed            */
 #define LBM_EUNSTABLE -4   /* the audit found non-finite populations                */
 #define LBM_ESTATE    -5   /* call out of order (e.g. lbm_step before lbm_init)      */
+#define LBM_EDEVICE   -6   /* a kernel gave up on a bounded wait (reported by sync)  */
 
 /* ---- models and storage forms ---- */
 #define LBM_D2Q33 0        /* Table 2: 33 velocities, 8 groups, reach 4 */
@@ -114,6 +115,22 @@ int lbm_destroy(lbm_ctx* ctx);
 /* lbm_set_omega - change the relaxation frequency (0 <= omega < 2) for later
  * steps; invalidates a recorded rollout.  Errors: LBM_EINVAL. */
 int lbm_set_omega(lbm_ctx* ctx, double omega);
+
+/*
+ * lbm_set_variant - choose the stream-collide kernel (same arithmetic, bitwise
+ * identical results):
+ *   0 (default) direct;
+ *   1 direct gather: one thread per cell loads its Q populations from HBM;
+ *   2 staged: persistent CTAs stream each 128-cell row segment of all Q shifted
+ *     source rows into shared memory with bulk asynchronous copies (mbarrier
+ *     pipeline, waits bounded at 2 s; a timeout sets the status that
+ *     lbm_synchronize reports as LBM_EDEVICE).  Needs Nx % 8 == 0;
+ *   3 split: the directions of each cell are divided between two warps that
+ *     exchange partial moments through shared memory (half the registers per
+ *     thread, twice the resident warps).  FP32 / FP16 / BF16 forms only.
+ * Errors: LBM_EINVAL.
+ */
+int lbm_set_variant(lbm_ctx* ctx, int variant);
 
 /* lbm_set_stream - order later calls on another stream of the same device. */
 int lbm_set_stream(lbm_ctx* ctx, void* stream);
@@ -203,7 +220,8 @@ int lbm_backward(lbm_ctx* ctx, const double* dL_drhoN, double* dL_drho0, double*
 /* lbm_release_record - free the checkpoints and segment buffers. */
 int lbm_release_record(lbm_ctx* ctx);
 
-/* lbm_synchronize - wait for all work on the context's stream. */
+/* lbm_synchronize - wait for all work on the context's stream; LBM_EDEVICE if
+ * a kernel of the context reported a timed-out wait. */
 int lbm_synchronize(lbm_ctx* ctx);
 
 /* lbm_launch_count - kernels this context has launched so far. */

@@ -69,7 +69,7 @@ int lbm_record(lbm_ctx* ctx, int64_t nsteps, int64_t ckpt_every) {
       dst = v.state[pp]->p;
       pp ^= 1;
     }
-    e = v.ops->step(v.model, cur, dst, v.g, v.omega, v.stream);
+    e = v.ops->step(v.model, cur, dst, v.g, v.omega, v.variant, v.status, v.stream);
     if (e != cudaSuccess) return ctx_cuda_fail(e, "stream_collide launch");
     *v.launches += 1;
     cur = dst;
@@ -138,7 +138,8 @@ int lbm_backward(lbm_ctx* ctx, const double* dL_drhoN, double* dL_drho0, double*
     states[0] = r.ckpt[c]->p;
     for (int64_t j = 1; j < s1 - s0; ++j) {
       states[j] = r.seg[j - 1]->p;
-      cudaError_t e = v.ops->step(v.model, states[j - 1], states[j], v.g, v.omega, v.stream);
+      cudaError_t e = v.ops->step(v.model, states[j - 1], states[j], v.g, v.omega, v.variant,
+                                   v.status, v.stream);
       if (e != cudaSuccess) return ctx_cuda_fail(e, "replay launch");
       *v.launches += 1;
     }

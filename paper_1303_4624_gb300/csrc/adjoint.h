@@ -55,6 +55,8 @@ struct CtxView {
   int64_t* steps;
   int64_t* launches;
   Record* rec;
+  int variant;      // stream-collide kernel variant the context uses
+  int* status;      // device status flag
 };
 
 int ctx_fail(int code, const char* msg);

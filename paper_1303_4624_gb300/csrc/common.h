@@ -21,6 +21,7 @@ struct ModelConst {
   float af;
   double c;
   double T0;           // 1 / (2 c^2), lattice units
+  int e[kMaxQc][3];    // lattice vectors in storage order (zero-padded to 3 components)
 };
 
 struct Grid {
@@ -35,8 +36,11 @@ struct StorageOps {
   cudaError_t (*upload)(const ModelConst* mc2);
   cudaError_t (*init)(int model, const double* rho, const double* U, const double* T, void* dst,
                       const Grid& g, cudaStream_t st);
+  // One stream-collide step.  variant: kVariantDirect or kVariantStaged (the caller
+  // checks kVariantStaged is applicable: Nx % 8 == 0).  status: device int set to 1
+  // if a staged launch gave up waiting for its copies.
   cudaError_t (*step)(int model, const void* src, void* dst, const Grid& g, double omega,
-                      cudaStream_t st);
+                      int variant, int* status, cudaStream_t st);
   cudaError_t (*moments)(int model, const void* src, const Grid& g, double* rho, double* U,
                          double* T, double* partials, cudaStream_t st);
   cudaError_t (*get_f)(int model, const void* src, double* f, const Grid& g, cudaStream_t st);
@@ -63,6 +67,11 @@ inline long long cell_blocks(const Grid& g) {
 cudaError_t launch_sum_reduce(const double* partials, long long n, double* out, cudaStream_t st);
 
 extern const StorageOps kOpsFP64, kOpsFP32, kOpsFP16, kOpsBF16;
+
+constexpr int kVariantDirect = 1;
+constexpr int kVariantStaged = 2;
+constexpr int kVariantSplit = 3;
+inline bool staged_applicable(const Grid& g) { return g.nx % 8 == 0; }
 
 constexpr int kAuditSlots = 8;
 constexpr int kMomentThreads = 256;

@@ -1,6 +1,8 @@
 // k_storage.inl - launchers of one storage form.  Included by k_fp64.cu,
 // k_fp32.cu, k_fp16.cu and k_bf16.cu after defining LBM_STORE (element type) and
 // LBM_OPS (name of the StorageOps table).
+#include <mutex>
+
 #include "kernels.cuh"
 
 namespace lbm {
@@ -21,8 +23,79 @@ cudaError_t init_m(const double* rho, const double* U, const double* T, void* ds
   return cudaGetLastError();
 }
 
+// Staged-kernel configuration per storage type: pipeline depth and CTAs per SM
+// (shared memory per CTA = STAGES * Q * (128 + 16) * sizeof(S)).
+template <class T>
+struct StagedCfg {
+  static constexpr int kStages = 2, kMinBlocks = 2;
+};
+template <>
+struct StagedCfg<double> {
+  static constexpr int kStages = 2, kMinBlocks = 1;
+};
+template <>
+struct StagedCfg<__half> {
+  static constexpr int kStages = 2, kMinBlocks = 4;
+};
+template <>
+struct StagedCfg<__nv_bfloat16> {
+  static constexpr int kStages = 2, kMinBlocks = 4;
+};
+
+struct LaunchCache {
+  int dev = -1;
+  int grid = 0;
+};
+
 template <int M>
-cudaError_t step_m(const void* src, void* dst, const Grid& g, double omega, cudaStream_t st) {
+cudaError_t step_staged_m(const void* src, void* dst, const Grid& g, double omega, int* status,
+                          cudaStream_t st) {
+  constexpr int STAGES = StagedCfg<S>::kStages, MINB = StagedCfg<S>::kMinBlocks;
+  using Lay = StageLayout<S, STAGES, Model<M>::Q>;
+  auto kern = k_stream_collide_staged<M, S, STAGES, MINB>;
+  static std::mutex mu;
+  static LaunchCache cache[16];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  int per_sm_grid;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    LaunchCache& lc = cache[dev & 15];
+    if (lc.dev != dev) {
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::kBytes);
+      if (e != cudaSuccess) return e;
+      int per_sm = 0, sms = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kStageW, Lay::kBytes);
+      if (e != cudaSuccess) return e;
+      e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e != cudaSuccess) return e;
+      if (per_sm < 1) return cudaErrorInvalidConfiguration;
+      lc.grid = per_sm * sms;
+      lc.dev = dev;
+    }
+    per_sm_grid = lc.grid;
+  }
+  const long long nchunks = (long long)((g.nx + kStageW - 1) / kStageW) * g.ny * g.nz;
+  const int grid = (int)(nchunks < per_sm_grid ? nchunks : per_sm_grid);
+  kern<<<grid, kStageW, Lay::kBytes, st>>>(static_cast<const S*>(src), static_cast<S*>(dst), g, omega,
+                                         (int)nchunks, status);
+  return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t step_m(const void* src, void* dst, const Grid& g, double omega, int variant, int* status,
+                   cudaStream_t st) {
+  if (variant == kVariantStaged) return step_staged_m<M>(src, dst, g, omega, status, st);
+  if constexpr (!std::is_same<S, double>::value) {
+    if (variant == kVariantSplit) {
+      constexpr int cells = kSplitThreads / 2;
+      const dim3 grid((unsigned)((g.nx + cells - 1) / cells), (unsigned)g.ny, (unsigned)g.nz);
+      k_stream_collide_split<M, S><<<grid, kSplitThreads, 0, st>>>(
+          static_cast<const S*>(src), static_cast<S*>(dst), g, omega);
+      return cudaGetLastError();
+    }
+  }
   const int bx = cell_block_x(g.nx);
   const dim3 grid((unsigned)((g.nx + bx - 1) / bx), (unsigned)g.ny, (unsigned)g.nz);
   k_stream_collide<M, S><<<grid, bx, 0, st>>>(static_cast<const S*>(src), static_cast<S*>(dst), g,
@@ -92,8 +165,10 @@ cudaError_t init(int m, const double* rho, const double* U, const double* T, voi
                  const Grid& g, cudaStream_t st) {
   return m == 0 ? init_m<0>(rho, U, T, dst, g, st) : init_m<1>(rho, U, T, dst, g, st);
 }
-cudaError_t step(int m, const void* src, void* dst, const Grid& g, double omega, cudaStream_t st) {
-  return m == 0 ? step_m<0>(src, dst, g, omega, st) : step_m<1>(src, dst, g, omega, st);
+cudaError_t step(int m, const void* src, void* dst, const Grid& g, double omega, int variant,
+                 int* status, cudaStream_t st) {
+  return m == 0 ? step_m<0>(src, dst, g, omega, variant, status, st)
+                : step_m<1>(src, dst, g, omega, variant, status, st);
 }
 cudaError_t moments(int m, const void* src, const Grid& g, double* rho, double* U, double* T,
                     double* partials, cudaStream_t st) {

@@ -102,151 +102,614 @@ __device__ __forceinline__ R gW(const ModelConst& mc, int g) {
   if constexpr (std::is_same<R, double>::value) return mc.W[g]; else return mc.Wf[g];
 }
 template <class R>
+__device__ __forceinline__ R gA(const ModelConst& mc) {
+  if constexpr (std::is_same<R, double>::value) return mc.a; else return mc.af;
+}
+template <class R>
 __device__ __forceinline__ R gX2(const ModelConst& mc, int g) {
   if constexpr (std::is_same<R, double>::value) return mc.X2[g]; else return mc.X2f[g];
 }
 
+// Explicitly rounded arithmetic for the stream-collide path.  The compiler never
+// fuses or reorders these (unlike a * b + c, which it may contract into an FMA
+// differently in each kernel), so every kernel variant performs the identical
+// operation sequence and their results agree bit for bit.
+template <class R>
+__device__ __forceinline__ R xadd(R a, R b) {
+  if constexpr (std::is_same<R, float>::value) return __fadd_rn(a, b); else return __dadd_rn(a, b);
+}
+template <class R>
+__device__ __forceinline__ R xsub(R a, R b) {
+  if constexpr (std::is_same<R, float>::value) return __fsub_rn(a, b); else return __dsub_rn(a, b);
+}
+template <class R>
+__device__ __forceinline__ R xmul(R a, R b) {
+  if constexpr (std::is_same<R, float>::value) return __fmul_rn(a, b); else return __dmul_rn(a, b);
+}
+template <class R>
+__device__ __forceinline__ R xfma(R a, R b, R c) {
+  if constexpr (std::is_same<R, float>::value) return __fmaf_rn(a, b, c); else return __fma_rn(a, b, c);
+}
+
+// A constant in the arithmetic type.
+template <class R>
+__device__ __forceinline__ R cst(double v) {
+  return (R)v;
+}
+
 // Kahan compensated accumulation: the running error is kept in c (true sum ~ s - c).
 __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
-  const float y = x - c;
-  const float t = s + y;
-  c = (t - s) - y;
+  const float y = __fsub_rn(x, c);
+  const float t = __fadd_rn(s, y);
+  c = __fsub_rn(__fsub_rn(t, s), y);
   s = t;
 }
 
-// Coefficients of A0, A1, A2 as functions of the group's x2 (see file header).
+// Coefficients of A0, A1, A2 as functions of the group's x2 (see file header):
+//   A0 - 1 = K0m1 + x2 (K1 + x2 K2),  A1 = L0 + L1 x2,  A2 = M0 + M1 x2, with
+//   K0m1 = q (q/8 - 1/2) + t (t D(D+2)/8 + q (D+2)/4 - D/2)   (A0 - 1 at x2 = 0,
+//          formed without the leading 1 so that P - 1 keeps the precision of the deviation)
+//   K1 = t (1/2 - q/4 - t (D+2)/4),  K2 = t^2/8,
+//   L0 = 1 - q/2 - t (D+2)/2,  L1 = t/2,  M0 = 1/2 - q/4 - t (D+4)/4,  M1 = t/4.
 template <class R, int D>
 struct EqCoef {
-  R K0, K1, K2, L0, L1, M0, M1;
+  R K0, K0m1, K1, K2, L0, L1, M0, M1;
   __device__ __forceinline__ EqCoef(R q, R t) {
-    K0 = R(1) - q * R(0.5) - t * R(0.5 * D) + q * q * R(0.125) + t * q * R(0.25 * (D + 2)) +
-         t * t * R(0.125 * D * (D + 2));
-    K1 = t * R(0.5) - t * q * R(0.25) - t * t * R(0.25 * (D + 2));
-    K2 = t * t * R(0.125);
-    L0 = R(1) - q * R(0.5) - t * R(0.5 * (D + 2));
-    L1 = t * R(0.5);
-    M0 = R(0.5) - q * R(0.25) - t * R(0.25 * (D + 4));
-    M1 = t * R(0.25);
+    K0m1 = xfma(t, xfma(t, cst<R>(0.125 * D * (D + 2)), xfma(q, cst<R>(0.25 * (D + 2)), cst<R>(-0.5 * D))),
+                xmul(q, xfma(q, cst<R>(0.125), cst<R>(-0.5))));
+    K0 = xadd(cst<R>(1), K0m1);
+    K1 = xmul(t, xfma(t, cst<R>(-0.25 * (D + 2)), xfma(q, cst<R>(-0.25), cst<R>(0.5))));
+    K2 = xmul(xmul(t, t), cst<R>(0.125));
+    L0 = xfma(t, cst<R>(-0.5 * (D + 2)), xfma(q, cst<R>(-0.5), cst<R>(1)));
+    L1 = xmul(t, cst<R>(0.5));
+    M0 = xfma(t, cst<R>(-0.25 * (D + 4)), xfma(q, cst<R>(-0.25), cst<R>(0.5)));
+    M1 = xmul(t, cst<R>(0.25));
   }
-  __device__ __forceinline__ R A0(R x2) const { return K0 + x2 * (K1 + x2 * K2); }
-  __device__ __forceinline__ R A1(R x2) const { return L0 + L1 * x2; }
-  __device__ __forceinline__ R A2(R x2) const { return M0 + M1 * x2; }
+  __device__ __forceinline__ R A0(R x2) const { return xfma(x2, xfma(x2, K2, K1), K0); }
+  __device__ __forceinline__ R A0m1(R x2) const { return xfma(x2, xfma(x2, K2, K1), K0m1); }
+  __device__ __forceinline__ R A1(R x2) const { return xfma(L1, x2, L0); }
+  __device__ __forceinline__ R A2(R x2) const { return xfma(M1, x2, M0); }
 };
 
+// s = e . v for a compile-time integer lattice vector e.
+template <class R, int EX, int EY, int EZ>
+__device__ __forceinline__ R edot(R vx, R vy, R vz) {
+  R s = cst<R>(0);
+  bool first = true;
+  if constexpr (EX != 0) { s = xmul(cst<R>(EX), vx); first = false; }
+  if constexpr (EY != 0) { s = first ? xmul(cst<R>(EY), vy) : xfma(cst<R>(EY), vy, s); first = false; }
+  if constexpr (EZ != 0) { s = first ? xmul(cst<R>(EZ), vz) : xfma(cst<R>(EZ), vz, s); }
+  return s;
+}
+
 // ----------------------------------------------------------------- fused stream-collide
-// One thread per cell, x fastest across the block; blockIdx.y / z give the row.
-// a1 pull-gather  g_i(x) = F_i((x - e_i) mod N)         (Q loads, coalesced along x)
-// a2 decode       f_i = w_i (1 + h_i)                    (kept as h_i)
+// Steps of one cell update (shared by the direct-gather and the staged kernel):
+// a1 pull-gather  g_i(x) = F_i((x - e_i) mod N)         (the caller's load functor)
+// a2 decode       f_i = w_i (1 + h_i), kept as h_i
 // a3 moments      rho - 1 = sum w_i h_i, j = sum w_i h_i xi_i, E - D = sum w_i h_i |xi_i|^2
-//                 (rest moments sum w = 1, sum w xi = 0, sum w |xi|^2 = D are exact)
-// a4 temperature  theta = (E/rho - |u|^2)/D in FP64
+//                 (the rest-state moments sum w = 1, sum w xi = 0, sum w |xi|^2 = D are
+//                 exact); opposite pairs are summed first; the rho and E sums are
+//                 Kahan-compensated in FP32
+// a4 temperature  theta - 1 = ((E - D rho) / rho - |u|^2) / D: the energy ratio and the
+//                 subtraction of the kinetic part are done in FP64 (FP64 reciprocal of rho
+//                 from the FP32 estimate by one step of Newton's method for 1/rho,
+//                 r' = r + r (1 - rho r), which squares the estimate's relative error)
 // a5 equilibrium  per group A0, A1, A2; per pair the even / odd parts in s
-// a6 BGK          h_i' = (1 - omega) h_i + omega (rho P_i - 1), stored at x
-template <int M, class S>
-__global__ void __launch_bounds__(128)
-    k_stream_collide(const S* __restrict__ src, S* __restrict__ dst, Grid g, double omega) {
+// a6 BGK          h_i' = (1 - omega) h_i + omega (rho P_i - 1), handed to the store functor
+// Partial moments of one half of the directions (rest + pairs [P0, P1) when REST).
+// Every kernel forms the moments as the same two halves, first [0, NP/2) with the
+// rest direction, then [NP/2, NP), combined in that order, so that the direct,
+// staged and split kernels produce bitwise identical results.
+template <class Rt>
+struct HalfMoments {
+  Rt rs, rc, es, ec, jx, jy, jz;   // Kahan sums (rs, es) with compensations (rc, ec)
+};
+
+// SHELL = false: every +/- pair's contribution enters the compensated rho and E sums.
+// SHELL = true (FP16 / BF16 forms): the equal-weight deviations of one symmetry
+// shell are first summed in plain FP32 (error ~ n 2^-24 |h|, far below the 2^-11
+// rounding of the stored values) and each shell's total enters the compensated
+// sums, so the compensation spans the five decades of weights across shells.
+template <int M, class Rt, int P0, int P1, bool REST, bool SHELL, class Get>
+__device__ __forceinline__ HalfMoments<Rt> half_moments(Get&& hv) {
+  using Mo = Model<M>;
+  const ModelConst& mc = c_mc[M];
+  HalfMoments<Rt> m;
+  m.rs = REST ? xmul(gW<Rt>(mc, 0), hv(std::integral_constant<int, 0>{})) : cst<Rt>(0);
+  m.rc = m.es = m.ec = m.jx = m.jy = m.jz = cst<Rt>(0);
+  Rt shell = cst<Rt>(0);
+  sfor<P0, P1>([&](auto P) {
+    constexpr int p = decltype(P)::value;
+    constexpr int ip = 1 + 2 * p, im = 2 + 2 * p;
+    constexpr int gg = Mo::vs.grp[ip];
+    constexpr int ex = Mo::vs.e[ip][0], ey = Mo::vs.e[ip][1], ez = Mo::vs.e[ip][2];
+    constexpr bool first = (p == P0) || (Mo::vs.grp[ip - 2] != gg);
+    constexpr bool last = (p + 1 == P1) || (Mo::vs.grp[ip + 2] != gg);
+    const Rt hp = hv(std::integral_constant<int, ip>{});
+    const Rt hm = hv(std::integral_constant<int, im>{});
+    const Rt sp = xadd(hp, hm);
+    if constexpr (SHELL) {
+      shell = first ? sp : xadd(shell, sp);
+      if constexpr (last) {
+        const Rt tr = xmul(gW<Rt>(mc, gg), shell);
+        kahan_add(m.rs, m.rc, tr);
+        kahan_add(m.es, m.ec, xmul(gX2<Rt>(mc, gg), tr));
+      }
+    } else {
+      const Rt tr = xmul(gW<Rt>(mc, gg), sp);
+      const Rt te = xmul(gX2<Rt>(mc, gg), tr);
+      if constexpr (!std::is_same<Rt, double>::value) {
+        kahan_add(m.rs, m.rc, tr);
+        kahan_add(m.es, m.ec, te);
+      } else {
+        m.rs = xadd(m.rs, tr);
+        m.es = xadd(m.es, te);
+      }
+    }
+    const Rt tj = xmul(gW<Rt>(mc, gg), xsub(hp, hm));
+    if constexpr (ex != 0) m.jx = xfma(cst<Rt>(ex), tj, m.jx);
+    if constexpr (ey != 0) m.jy = xfma(cst<Rt>(ey), tj, m.jy);
+    if constexpr (ez != 0) m.jz = xfma(cst<Rt>(ez), tj, m.jz);
+  });
+  return m;
+}
+
+// Cell state from the two halves: FP64 theta recovery, FP32 (or FP64) velocity.
+template <class Rt>
+struct CellState {
+  Rt q, t, uax, uay, uaz;   // |u|^2, theta - 1, a u
+  Rt rho, rdev;             // rho, rho - 1
+  Rt wr, wrd;               // omega rho, omega (rho - 1)
+};
+
+template <int M, class Rt>
+__device__ __forceinline__ CellState<Rt> cell_state(const HalfMoments<Rt>& A,
+                                                    const HalfMoments<Rt>& B, double omega) {
+  constexpr int D = Model<M>::D;
+  const ModelConst& mc = c_mc[M];
+  CellState<Rt> c;
+  double rd, ed, ir;
+  Rt jx, jy, jz, rho_r, ir_r;
+  if constexpr (std::is_same<Rt, float>::value) {
+    rd = xadd(xsub((double)A.rs, (double)A.rc), xsub((double)B.rs, (double)B.rc));
+    ed = xadd(xsub((double)A.es, (double)A.ec), xsub((double)B.es, (double)B.ec));
+    jx = xadd(A.jx, B.jx);
+    jy = xadd(A.jy, B.jy);
+    jz = xadd(A.jz, B.jz);
+    const double rho_d = xadd(1.0, rd);
+    rho_r = (float)rho_d;
+    ir = (double)__fdividef(1.0f, rho_r);
+    ir = xfma(ir, xfma(-rho_d, ir, 1.0), ir);     // Newton's method for 1/rho
+    ir_r = (float)ir;                             // 1/rho rounded to FP32
+  } else {
+    rd = xadd(A.rs, B.rs);
+    ed = xadd(A.es, B.es);
+    jx = xadd(A.jx, B.jx);
+    jy = xadd(A.jy, B.jy);
+    jz = xadd(A.jz, B.jz);
+    rho_r = xadd(1.0, rd);
+    ir_r = 1.0 / rho_r;
+    ir = ir_r;
+  }
+  const Rt a = gA<Rt>(mc);
+  const Rt ux = xmul(xmul(a, jx), ir_r), uy = xmul(xmul(a, jy), ir_r);
+  const Rt uz = (D == 3) ? xmul(xmul(a, jz), ir_r) : Rt(0);
+  c.q = xfma(ux, ux, xfma(uy, uy, xmul(uz, uz)));
+  // theta - 1 = ((E - D rho) / rho - |u|^2) / D, in FP64
+  c.t = (Rt)xmul(xfma(xfma(-(double)D, rd, ed), ir, -(double)c.q), 1.0 / D);
+  c.uax = xmul(a, ux);
+  c.uay = xmul(a, uy);
+  c.uaz = xmul(a, uz);
+  c.rho = rho_r;
+  c.rdev = (Rt)rd;
+  c.wr = xmul((Rt)omega, rho_r);
+  c.wrd = (Rt)xmul(omega, rd);
+  return c;
+}
+
+// Equilibrium + BGK of pairs [P0, P1) (and the rest direction when REST), with
+// h_i^eq = (rho - 1) + rho (P_i - 1):
+//   EXACT = true:  h_i' = h_i + omega (h_i^eq - h_i)   (FP32 / FP64 forms).  The
+//                  equilibrium is an exact fixed point whatever the rounding of omega;
+//                  with (1 - omega) h + omega h^eq the two rounded factors need not
+//                  sum to one and a uniform region drifts by their difference every
+//                  step (about 1e-5 in rho after 200 steps at omega = 1.8 in FP32).
+//   EXACT = false: h_i' = (1 - omega) h_i + omega (rho - 1) + omega rho (P_i - 1)
+//                  (FP16 / BF16 forms: two instructions fewer per pair; the drift is
+//                  far below the storage rounding).
+template <int M, class Rt, int P0, int P1, bool REST, bool EXACT, class Get, class Store>
+__device__ __forceinline__ void half_collide(const CellState<Rt>& c, double omega, Get&& hv,
+                                             Store&& st) {
+  using Mo = Model<M>;
+  constexpr int D = Mo::D;
+  const ModelConst& mc = c_mc[M];
+  const EqCoef<Rt, D> cf(c.q, c.t);
+  const Rt om = cst<Rt>(omega);
+  const Rt om1 = cst<Rt>(1.0 - omega);
+  if constexpr (REST) {
+    const Rt h0 = hv(std::integral_constant<int, 0>{});
+    if constexpr (EXACT)
+      st(std::integral_constant<int, 0>{}, xfma(om, xsub(xfma(c.rho, cf.K0m1, c.rdev), h0), h0));
+    else
+      st(std::integral_constant<int, 0>{}, xfma(om1, h0, xfma(c.wr, cf.K0m1, c.wrd)));
+  }
+  sfor<P0, P1>([&](auto P) {
+    constexpr int p = decltype(P)::value;
+    constexpr int ip = 1 + 2 * p, im = 2 + 2 * p;
+    constexpr int gg = Mo::vs.grp[ip];
+    constexpr int ex = Mo::vs.e[ip][0], ey = Mo::vs.e[ip][1], ez = Mo::vs.e[ip][2];
+    const Rt x2 = gX2<Rt>(mc, gg);
+    const Rt s = edot<Rt, ex, ey, ez>(c.uax, c.uay, c.uaz);
+    const Rt s2 = xmul(s, s);
+    const Rt ev = xfma(s2, xfma(s2, cst<Rt>(1.0 / 24.0), cf.A2(x2)), cf.A0m1(x2));
+    const Rt od = xmul(s, xfma(s2, cst<Rt>(1.0 / 6.0), cf.A1(x2)));
+    const Rt hp = hv(std::integral_constant<int, ip>{});
+    const Rt hm = hv(std::integral_constant<int, im>{});
+    if constexpr (EXACT) {
+      const Rt be = xfma(c.rho, ev, c.rdev);      // even part of h^eq
+      const Rt bo = xmul(c.rho, od);              // odd part of h^eq
+      st(std::integral_constant<int, ip>{}, xfma(om, xsub(xadd(be, bo), hp), hp));
+      st(std::integral_constant<int, im>{}, xfma(om, xsub(xsub(be, bo), hm), hm));
+    } else {
+      const Rt base = xfma(c.wr, ev, c.wrd);
+      const Rt wod = xmul(c.wr, od);
+      st(std::integral_constant<int, ip>{}, xfma(om1, hp, xadd(base, wod)));
+      st(std::integral_constant<int, im>{}, xfma(om1, hm, xsub(base, wod)));
+    }
+  });
+}
+
+// Arithmetic options per storage form: FP32 / FP64 storage keep per-pair Kahan sums
+// and the exact-fixed-point relaxation; FP16 / BF16 storage use per-shell
+// compensation and the two-term relaxation (see half_moments / half_collide).
+template <class S>
+struct FormOpts {
+  static constexpr bool kShell = sizeof(S) == 2;
+  static constexpr bool kExact = sizeof(S) >= 4;
+};
+
+template <int M, class S, class Load, class Store>
+__device__ __forceinline__ void cell_update(Load&& ld, double omega, Store&& st) {
   using Mo = Model<M>;
   using Rt = typename Codec<S>::R;
-  constexpr int Q = Mo::Q, D = Mo::D, RR = Mo::R, NP = Mo::NP, G = Mo::G;
-  constexpr bool kComp = std::is_same<Rt, float>::value;
-  const ModelConst& mc = c_mc[M];
+  constexpr int Q = Mo::Q, NP = Mo::NP, NH = NP / 2;
+  constexpr bool SH = FormOpts<S>::kShell, EX = FormOpts<S>::kExact;
+  // a1 + a2
+  Rt h[Q];
+  sfor<0, Q>([&](auto I) { h[decltype(I)::value] = ld(I); });
+  auto hv = [&](auto I) { return h[decltype(I)::value]; };
+  // a3, a4
+  const HalfMoments<Rt> A = half_moments<M, Rt, 0, NH, true, SH>(hv);
+  const HalfMoments<Rt> B = half_moments<M, Rt, NH, NP, false, SH>(hv);
+  const CellState<Rt> c = cell_state<M, Rt>(A, B, omega);
+  // a5, a6
+  half_collide<M, Rt, 0, NH, true, EX>(c, omega, hv, st);
+  half_collide<M, Rt, NH, NP, false, EX>(c, omega, hv, st);
+}
 
+// Periodic index for -n <= v < 2n (one correction each way).
+__device__ __forceinline__ int wrap1(int v, int n) {
+  v += (v < 0) ? n : 0;
+  v -= (v >= n) ? n : 0;
+  return v;
+}
+
+// Direct-gather kernel: one thread per cell, x fastest across the block,
+// blockIdx.y / z give the row; Q loads per thread straight from HBM / L2.
+// LBM_DIRECT_MINB: resident 128-thread blocks per SM the register budget is cut
+// for (128 registers at 4: 16 warps per SM; measured best for the FP32 and FP16
+// forms).  The FP64 form keeps 2 (its 95 doubles need 190 registers).
+#ifndef LBM_DIRECT_MINB
+#define LBM_DIRECT_MINB 4
+#endif
+template <class S>
+struct DirectMinBlocks {
+  static constexpr int value = std::is_same<S, double>::value ? 2 : LBM_DIRECT_MINB;
+};
+template <int M, class S>
+__global__ void __launch_bounds__(128, DirectMinBlocks<S>::value)
+    k_stream_collide(const S* __restrict__ src, S* __restrict__ dst, Grid g, double omega) {
+  using Mo = Model<M>;
+  constexpr int D = Mo::D, RR = Mo::R;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= g.nx) return;
   const int y = blockIdx.y, z = blockIdx.z;
-
   int xo[2 * RR + 1], yo[2 * RR + 1], zo[2 * RR + 1];
-  sfor<0, 2 * RR + 1>([&](auto K) {
-    constexpr int k = decltype(K)::value;
-    xo[k] = wrapi(x - (k - RR), g.nx);
-    yo[k] = wrapi(y - (k - RR), g.ny) * g.nx;
-    if constexpr (D == 3) zo[k] = wrapi(z - (k - RR), g.nz) * g.nxy; else zo[k] = 0;
-  });
+  if (g.nx >= RR && g.ny >= RR && g.nz >= RR) {
+    sfor<0, 2 * RR + 1>([&](auto K) {
+      constexpr int k = decltype(K)::value;
+      xo[k] = wrap1(x - (k - RR), g.nx);
+      yo[k] = wrap1(y - (k - RR), g.ny) * g.nx;
+      if constexpr (D == 3) zo[k] = wrap1(z - (k - RR), g.nz) * g.nxy; else zo[k] = 0;
+    });
+  } else {
+    sfor<0, 2 * RR + 1>([&](auto K) {
+      constexpr int k = decltype(K)::value;
+      xo[k] = wrapi(x - (k - RR), g.nx);
+      yo[k] = wrapi(y - (k - RR), g.ny) * g.nx;
+      if constexpr (D == 3) zo[k] = wrapi(z - (k - RR), g.nz) * g.nxy; else zo[k] = 0;
+    });
+  }
+  const size_t self = ((size_t)z * g.ny + y) * g.nx + x;
+  cell_update<M, S>(
+      [&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int ex = Mo::vs.e[i][0], ey = Mo::vs.e[i][1], ez = Mo::vs.e[i][2];
+        const int cell = zo[ez + RR] + yo[ey + RR] + xo[ex + RR];
+        return Codec<S>::ld(src + (size_t)i * (size_t)g.ncell + cell);
+      },
+      omega,
+      [&](auto I, typename Codec<S>::R v) {
+        Codec<S>::st(dst + (size_t)decltype(I)::value * (size_t)g.ncell + self, v);
+      });
+}
 
-  // a1 + a2: gather
-  Rt h[Q];
-  sfor<0, Q>([&](auto I) {
+// ----------------------------------------------------------------- split kernel
+// Warp-pair kernel: the Q directions of each cell are split between two warps that
+// handle the same 32 cells (warp 2k: the rest direction and pairs [0, NP/2), warp
+// 2k+1: pairs [NP/2, NP)), which halves the registers a thread holds and doubles
+// the warps an SM keeps resident.  Each warp forms the partial moments of its
+// half; the two halves are exchanged through shared memory behind a named
+// 64-thread barrier and combined in a fixed order (first half, then second), so
+// both warps hold identical moments; each then evaluates the equilibrium and the
+// BGK update for its own directions.  Same arithmetic per direction as cell_update.
+#ifndef LBM_SPLIT_MINB
+#define LBM_SPLIT_MINB 3
+#endif
+constexpr int kSplitThreads = 256;                 // 4 warp pairs = 128 cells per block
+
+__device__ __forceinline__ void pair_barrier(int id) {
+  asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory");
+}
+
+template <int M, class S, int HALF, class Load, class Store>
+__device__ __forceinline__ void half_update(Load&& ld, double omega, Store&& st,
+                                            float (*xch)[2][8][32], int pair, int lane) {
+  using Mo = Model<M>;
+  using Rt = typename Codec<S>::R;
+  static_assert(std::is_same<Rt, float>::value, "split kernel is for the FP32-arithmetic forms");
+  constexpr int NP = Mo::NP, NH = NP / 2;
+  constexpr int P0 = HALF == 0 ? 0 : NH, P1 = HALF == 0 ? NH : NP;
+  constexpr int I0 = HALF == 0 ? 0 : 1 + 2 * NH;   // first direction index of this half
+  constexpr int NV = 1 + 2 * P1 - I0;               // directions held by this half
+  Rt h[NV];
+  sfor<I0, 1 + 2 * P1>([&](auto I) { h[decltype(I)::value - I0] = ld(I); });
+  auto hv = [&](auto I) { return h[decltype(I)::value - I0]; };
+  const HalfMoments<Rt> mine = half_moments<M, Rt, P0, P1, HALF == 0, FormOpts<S>::kShell>(hv);
+  // exchange the partial moments of the two halves
+  float* w = &xch[pair][HALF][0][lane];
+  w[0] = mine.rs; w[32] = mine.rc; w[64] = mine.es; w[96] = mine.ec;
+  w[128] = mine.jx; w[160] = mine.jy; w[192] = mine.jz;
+  pair_barrier(1 + pair);
+  HalfMoments<Rt> A, B;
+  const float* a = &xch[pair][0][0][lane];
+  const float* b = &xch[pair][1][0][lane];
+  A.rs = a[0]; A.rc = a[32]; A.es = a[64]; A.ec = a[96]; A.jx = a[128]; A.jy = a[160]; A.jz = a[192];
+  B.rs = b[0]; B.rc = b[32]; B.es = b[64]; B.ec = b[96]; B.jx = b[128]; B.jy = b[160]; B.jz = b[192];
+  const CellState<Rt> c = cell_state<M, Rt>(A, B, omega);
+  half_collide<M, Rt, P0, P1, HALF == 0, FormOpts<S>::kExact>(c, omega, hv, st);
+}
+
+template <int M, class S>
+__global__ void __launch_bounds__(kSplitThreads, LBM_SPLIT_MINB)
+    k_stream_collide_split(const S* __restrict__ src, S* __restrict__ dst, Grid g, double omega) {
+  using Mo = Model<M>;
+  constexpr int D = Mo::D, RR = Mo::R;
+  __shared__ float xch[kSplitThreads / 64][2][8][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int pair = warp >> 1, half = warp & 1;
+  const int xw = blockIdx.x * (kSplitThreads / 2) + pair * 32;   // first cell of the pair
+  if (xw >= g.nx) return;                                        // the whole pair is idle
+  const int x = xw + lane;
+  const bool active = x < g.nx;
+  const int y = blockIdx.y, z = blockIdx.z;
+  int xo[2 * RR + 1], yo[2 * RR + 1], zo[2 * RR + 1];
+  const int xa = active ? x : xw;
+  if (g.nx >= RR && g.ny >= RR && g.nz >= RR) {
+    sfor<0, 2 * RR + 1>([&](auto K) {
+      constexpr int k = decltype(K)::value;
+      xo[k] = wrap1(xa - (k - RR), g.nx);
+      yo[k] = wrap1(y - (k - RR), g.ny) * g.nx;
+      if constexpr (D == 3) zo[k] = wrap1(z - (k - RR), g.nz) * g.nxy; else zo[k] = 0;
+    });
+  } else {
+    sfor<0, 2 * RR + 1>([&](auto K) {
+      constexpr int k = decltype(K)::value;
+      xo[k] = wrapi(xa - (k - RR), g.nx);
+      yo[k] = wrapi(y - (k - RR), g.ny) * g.nx;
+      if constexpr (D == 3) zo[k] = wrapi(z - (k - RR), g.nz) * g.nxy; else zo[k] = 0;
+    });
+  }
+  const size_t self = ((size_t)z * g.ny + y) * g.nx + xa;
+  auto ld = [&](auto I) {
     constexpr int i = decltype(I)::value;
     constexpr int ex = Mo::vs.e[i][0], ey = Mo::vs.e[i][1], ez = Mo::vs.e[i][2];
     const int cell = zo[ez + RR] + yo[ey + RR] + xo[ex + RR];
-    h[i] = Codec<S>::ld(src + (size_t)i * (size_t)g.ncell + cell);
-  });
+    return Codec<S>::ld(src + (size_t)i * (size_t)g.ncell + cell);
+  };
+  auto st = [&](auto I, float v) {
+    if (active) Codec<S>::st(dst + (size_t)decltype(I)::value * (size_t)g.ncell + self, v);
+  };
+  if (half == 0)
+    half_update<M, S, 0>(ld, omega, st, xch, pair, lane);
+  else
+    half_update<M, S, 1>(ld, omega, st, xch, pair, lane);
+}
 
-  // a3: moments (deviation form)
-  Rt rs = gW<Rt>(mc, 0) * h[0], rc = Rt(0), es = Rt(0), ec = Rt(0);
-  Rt jx = Rt(0), jy = Rt(0), jz = Rt(0);
-  sfor<0, NP>([&](auto P) {
-    constexpr int p = decltype(P)::value;
-    constexpr int ip = 1 + 2 * p, im = 2 + 2 * p;
-    constexpr int gg = Mo::vs.grp[ip];
-    constexpr int ex = Mo::vs.e[ip][0], ey = Mo::vs.e[ip][1], ez = Mo::vs.e[ip][2];
-    const Rt sp = h[ip] + h[im];
-    const Rt dm = h[ip] - h[im];
-    const Rt tr = gW<Rt>(mc, gg) * sp;
-    const Rt te = gX2<Rt>(mc, gg) * tr;
-    if constexpr (kComp) {
-      kahan_add(rs, rc, tr);
-      kahan_add(es, ec, te);
-    } else {
-      rs += tr;
-      es += te;
-    }
-    const Rt tj = gW<Rt>(mc, gg) * dm;
-    if constexpr (ex != 0) jx += Rt(ex) * tj;
-    if constexpr (ey != 0) jy += Rt(ey) * tj;
-    if constexpr (ez != 0) jz += Rt(ez) * tj;
-  });
+// ----------------------------------------------------------------- staged (TMA bulk) kernel
+// Persistent CTAs of kStageW threads walk "chunks" (kStageW consecutive cells of one
+// x-row).  For each chunk, warp 0 streams the kStageW + 2 kStagePad elements of every
+// direction's source row (the shifted plane of that direction: row (y - e_y, z - e_z),
+// x from x0 - kStagePad, periodic) from HBM into shared memory with cp.async.bulk,
+// completing on the stage's mbarrier; STAGES chunks are in flight.  Each thread then
+// reads its Q populations at compile-time offsets (no address arithmetic), updates the
+// cell, and stores the Q results.  Needs Nx a multiple of 8 (16-byte copies).
+constexpr int kStageW = 128;
+constexpr int kStagePad = 8;
 
-  // a4: FP64 temperature recovery
-  const double rho = 1.0 + ((double)rs - (double)rc);
-  const double E = (double)D + ((double)es - (double)ec);
-  const double ir = 1.0 / rho;
-  const double ux = mc.a * (double)jx * ir;
-  const double uy = mc.a * (double)jy * ir;
-  const double uz = (D == 3) ? mc.a * (double)jz * ir : 0.0;
-  const double qd = ux * ux + uy * uy + uz * uz;
-  const double theta = (E * ir - qd) * (1.0 / D);
-
-  // a5 + a6: equilibrium and BGK
-  const EqCoef<Rt, D> cf((Rt)qd, (Rt)(theta - 1.0));
-  const Rt uax = (Rt)(mc.a * ux), uay = (Rt)(mc.a * uy), uaz = (Rt)(mc.a * uz);
-  const Rt om1 = (Rt)(1.0 - omega);
-  const Rt wr = (Rt)(omega * rho);
-  const Rt nw = (Rt)(-omega);
-  const size_t self = ((size_t)z * g.ny + y) * g.nx + x;
-
-  Rt A0[G], A1[G], A2[G];
-  sfor<0, G>([&](auto GG) {
-    constexpr int gg = decltype(GG)::value;
-    const Rt x2 = gX2<Rt>(mc, gg);
-    A0[gg] = cf.A0(x2);
-    A1[gg] = cf.A1(x2);
-    A2[gg] = cf.A2(x2);
-  });
-
-  {
-    const Rt hn = om1 * h[0] + (wr * cf.K0 + nw);
-    Codec<S>::st(dst + self, hn);
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for an mbarrier phase, giving up after limit_ns of wall time.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (true) {
+    for (int k = 0; k < 64; ++k)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > limit_ns) return false;
   }
-  sfor<0, NP>([&](auto P) {
-    constexpr int p = decltype(P)::value;
-    constexpr int ip = 1 + 2 * p, im = 2 + 2 * p;
-    constexpr int gg = Mo::vs.grp[ip];
-    constexpr int ex = Mo::vs.e[ip][0], ey = Mo::vs.e[ip][1], ez = Mo::vs.e[ip][2];
-    Rt s = Rt(0);
-    if constexpr (ex != 0) s += Rt(ex) * uax;
-    if constexpr (ey != 0) s += Rt(ey) * uay;
-    if constexpr (ez != 0) s += Rt(ez) * uaz;
-    const Rt s2 = s * s;
-    const Rt ev = s2 * (s2 * Rt(1.0 / 24.0) + A2[gg]) + A0[gg];
-    const Rt od = s * (s2 * Rt(1.0 / 6.0) + A1[gg]);
-    const Rt base = wr * ev + nw;
-    const Rt wod = wr * od;
-    const Rt hp = om1 * h[ip] + (base + wod);
-    const Rt hm = om1 * h[im] + (base - wod);
-    Codec<S>::st(dst + (size_t)ip * (size_t)g.ncell + self, hp);
-    Codec<S>::st(dst + (size_t)im * (size_t)g.ncell + self, hm);
-  });
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+template <class S>
+__device__ __forceinline__ typename Codec<S>::R lds(const S* p) {
+  if constexpr (std::is_same<S, __half>::value)
+    return __half2float(*p);
+  else if constexpr (std::is_same<S, __nv_bfloat16>::value)
+    return __bfloat162float(*p);
+  else
+    return *p;
+}
+
+template <class S, int STAGES, int Q>
+struct StageLayout {
+  static constexpr int kRow = kStageW + 2 * kStagePad;      // elements per staged row
+  static constexpr int kStageElems = Q * kRow;
+  static constexpr size_t kDataBytes = (size_t)STAGES * kStageElems * sizeof(S);
+  static constexpr size_t kBytes = kDataBytes + STAGES * sizeof(unsigned long long);
+};
+
+template <int M, class S, int STAGES, int MINB>
+__global__ void __launch_bounds__(kStageW, MINB)
+    k_stream_collide_staged(const S* __restrict__ src, S* __restrict__ dst, Grid g, double omega,
+                            int nchunks, int* __restrict__ status) {
+  using Mo = Model<M>;
+  constexpr int Q = Mo::Q;
+  using L = StageLayout<S, STAGES, Q>;
+  constexpr uint64_t kLimitNs = 2000000000ull;    // 2 s: far beyond any real copy latency
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  S* stage_mem = reinterpret_cast<S*>(smem_raw);
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem_raw + L::kDataBytes);
+  __shared__ int sdir[Q][3];
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < Q; i += blockDim.x) {
+    sdir[i][0] = c_mc[M].e[i][0];
+    sdir[i][1] = c_mc[M].e[i][1];
+    sdir[i][2] = c_mc[M].e[i][2];
+  }
+  if (tid == 0) {
+    for (int s = 0; s < STAGES; ++s) mbar_init(smem_addr(&bars[s]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  const int nxc = (g.nx + kStageW - 1) / kStageW;
+  auto issue = [&](int c, int stage) {   // executed by all lanes of warp 0
+    const int xc = c % nxc, row = c / nxc;
+    const int y = row % g.ny, z = row / g.ny;
+    const int x0 = xc * kStageW;
+    const int wc = min(kStageW, g.nx - x0);
+    const uint32_t bar = smem_addr(&bars[stage]);
+    if (lane == 0) mbar_expect_tx(bar, (uint32_t)(Q * (wc + 2 * kStagePad) * sizeof(S)));
+    __syncwarp();
+    for (int i = lane; i < Q; i += 32) {
+      const int ys = wrapi(y - sdir[i][1], g.ny);
+      const int zs = wrapi(z - sdir[i][2], g.nz);
+      const S* rowp = src + (size_t)i * (size_t)g.ncell + ((size_t)zs * g.ny + ys) * g.nx;
+      const uint32_t d0 = smem_addr(stage_mem + (size_t)stage * L::kStageElems + (size_t)i * L::kRow);
+      int xlo = x0 - kStagePad;
+      const int xhi = x0 + wc + kStagePad;
+      int j = 0;
+      if (xlo < 0) {
+        bulk_g2s(d0, rowp + (g.nx + xlo), (uint32_t)(-xlo * sizeof(S)), bar);
+        j = -xlo;
+        xlo = 0;
+      }
+      const int mhi = min(xhi, g.nx);
+      bulk_g2s(d0 + j * sizeof(S), rowp + xlo, (uint32_t)((mhi - xlo) * sizeof(S)), bar);
+      j += mhi - xlo;
+      if (xhi > g.nx) bulk_g2s(d0 + j * sizeof(S), rowp, (uint32_t)((xhi - g.nx) * sizeof(S)), bar);
+    }
+  };
+
+  const int G = gridDim.x;
+  if (warp == 0)
+    for (int s = 0; s < STAGES - 1; ++s) {
+      const int c = blockIdx.x + s * G;
+      if (c < nchunks) issue(c, s);
+    }
+  int k = 0;
+  bool failed = false;
+  for (int c = blockIdx.x; c < nchunks; c += G, ++k) {
+    const int stage = k % STAGES;
+    if (warp == 0) {
+      const int cn = c + (STAGES - 1) * G;
+      if (cn < nchunks) issue(cn, (k + STAGES - 1) % STAGES);
+    }
+    const bool ok = mbar_wait_bounded(smem_addr(&bars[stage]), (uint32_t)((k / STAGES) & 1), kLimitNs);
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    const int xc = c % nxc, row = c / nxc;
+    const int x0 = xc * kStageW;
+    if (tid < min(kStageW, g.nx - x0)) {
+      const S* sp = stage_mem + (size_t)stage * L::kStageElems + kStagePad + tid;
+      const size_t self = (size_t)row * g.nx + x0 + tid;
+      cell_update<M, S>(
+          [&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int off = i * L::kRow - Mo::vs.e[i][0];
+            return lds<S>(sp + off);
+          },
+          omega,
+          [&](auto I, typename Codec<S>::R v) {
+            Codec<S>::st(dst + (size_t)decltype(I)::value * (size_t)g.ncell + self, v);
+          });
+    }
+    __syncthreads();   // the stage is consumed: it may be refilled
+  }
+  if (failed && tid == 0) {
+    atomicExch(status, 1);
+    // drain the copies this CTA still has in flight before its shared memory goes away
+    for (int j = 1; j < STAGES; ++j) {
+      const int kk = k + j;
+      const int cc = blockIdx.x + kk * G;
+      if (cc < nchunks) mbar_wait_bounded(smem_addr(&bars[kk % STAGES]), (uint32_t)((kk / STAGES) & 1), kLimitNs);
+    }
+  }
 }
 
 // ----------------------------------------------------------------- equilibrium init (FP64)
@@ -451,14 +914,21 @@ __device__ __forceinline__ double block_sum_128(double v, double* sh) {
   return r;
 }
 
+#ifndef LBM_ADJ_MINB
+#define LBM_ADJ_MINB 2
+#endif
+template <class S>
+struct AdjMinBlocks {
+  static constexpr int value = std::is_same<S, double>::value ? 1 : LBM_ADJ_MINB;
+};
 template <int M, class S, class L, bool kFirst>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, AdjMinBlocks<S>::value)
     k_adjoint(const S* __restrict__ state, const L* __restrict__ nu_next,
               const double* __restrict__ dldrho, L* __restrict__ nu_out,
               double* __restrict__ omega_acc, Grid g, double omega) {
   using Mo = Model<M>;
   using Rt = L;
-  constexpr int Q = Mo::Q, D = Mo::D, RR = Mo::R, NP = Mo::NP, G = Mo::G;
+  constexpr int Q = Mo::Q, D = Mo::D, RR = Mo::R, NP = Mo::NP;
   const ModelConst& mc = c_mc[M];
   __shared__ double sh[4];
 
@@ -512,17 +982,37 @@ __global__ void __launch_bounds__(128)
       if constexpr (ez != 0) jz += Rt(ez) * tj;
       sg += w * (lam[ip] * (Rt(1) + hp) + lam[im] * (Rt(1) + hm));
     });
-    const double rho = 1.0 + ((double)rs - (double)rc);
-    const double E = (double)D + ((double)es - (double)ec);
-    const double ir = 1.0 / rho;
-    const double ux = mc.a * (double)jx * ir, uy = mc.a * (double)jy * ir;
-    const double uz = (D == 3) ? mc.a * (double)jz * ir : 0.0;
-    const double qd = ux * ux + uy * uy + uz * uz;
-    const double theta = (E * ir - qd) * (1.0 / D);
-    const Rt q = (Rt)qd, t = (Rt)(theta - 1.0);
+    // forward moments and temperature, as in the forward step (FP64 only for theta - 1)
+    Rt q, t, ux, uy, uz, rho_r, ir_r;
+    double rho_d;
+    if constexpr (std::is_same<Rt, float>::value) {
+      rho_r = 1.0f + (rs - rc);
+      ir_r = __fdividef(1.0f, rho_r);
+      ux = mc.af * jx * ir_r;
+      uy = mc.af * jy * ir_r;
+      uz = (D == 3) ? mc.af * jz * ir_r : 0.0f;
+      q = ux * ux + uy * uy + uz * uz;
+      const double rd = (double)rs - (double)rc;
+      const double ed = (double)es - (double)ec;
+      rho_d = 1.0 + rd;
+      double ir = (double)ir_r;
+      ir = fma(ir, fma(-rho_d, ir, 1.0), ir);
+      t = (float)(fma(fma(-(double)D, rd, ed), ir, -(double)q) * (1.0 / D));
+    } else {
+      rho_d = 1.0 + rs;
+      rho_r = rho_d;
+      ir_r = 1.0 / rho_d;
+      ux = mc.a * jx * ir_r;
+      uy = mc.a * jy * ir_r;
+      uz = (D == 3) ? mc.a * jz * ir_r : 0.0;
+      q = ux * ux + uy * uy + uz * uz;
+      t = ((es - (double)D * rs) * ir_r - q) * (1.0 / D);
+    }
+    const Rt theta = Rt(1) + t;
     const EqCoef<Rt, D> cf(q, t);
     const EqGrad<Rt, D> gr(q, t);
-    const Rt uax = (Rt)(mc.a * ux), uay = (Rt)(mc.a * uy), uaz = (Rt)(mc.a * uz);
+    const Rt a_r = gA<Rt>(mc);
+    const Rt uax = a_r * ux, uay = a_r * uy, uaz = a_r * uz;
 
     // pass 2: contractions with lambda
     Rt Lr = gW<Rt>(mc, 0) * lam[0] * cf.K0;
@@ -559,24 +1049,24 @@ __global__ void __launch_bounds__(128)
       if constexpr (ey != 0) Vy += Rt(ey) * v;
       if constexpr (ez != 0) Vz += Rt(ez) * v;
     });
-    // chain rule to the moments (FP64 scalars)
-    const double Lux = rho * (mc.a * (double)Vx + 2.0 * ux * (double)Sq);
-    const double Luy = rho * (mc.a * (double)Vy + 2.0 * uy * (double)Sq);
-    const double Luz = (D == 3) ? rho * (mc.a * (double)Vz + 2.0 * uz * (double)Sq) : 0.0;
-    const double Lt = rho * (double)St;
-    const double iDr = ir * (1.0 / D);
-    const double alpha = (double)Lr - (ux * Lux + uy * Luy + uz * Luz) * ir + Lt * (qd - D * theta) * iDr;
-    const double bx = Lux * ir - 2.0 * Lt * ux * iDr;
-    const double by = Luy * ir - 2.0 * Lt * uy * iDr;
-    const double bz = Luz * ir - 2.0 * Lt * uz * iDr;
-    const double gam = Lt * iDr;
-    om_part = rho * (double)Lr - (double)sg;
+    // chain rule to the moments (arithmetic type; the omega term in FP64)
+    const Rt Lux = rho_r * (a_r * Vx + Rt(2) * ux * Sq);
+    const Rt Luy = rho_r * (a_r * Vy + Rt(2) * uy * Sq);
+    const Rt Luz = (D == 3) ? rho_r * (a_r * Vz + Rt(2) * uz * Sq) : Rt(0);
+    const Rt Lt = rho_r * St;
+    const Rt iDr = ir_r * Rt(1.0 / D);
+    const Rt alpha = Lr - (ux * Lux + uy * Luy + uz * Luz) * ir_r + Lt * (q - Rt(D) * theta) * iDr;
+    const Rt bx = Lux * ir_r - Rt(2) * Lt * ux * iDr;
+    const Rt by = Luy * ir_r - Rt(2) * Lt * uy * iDr;
+    const Rt bz = Luz * ir_r - Rt(2) * Lt * uz * iDr;
+    const Rt gam = Lt * iDr;
+    om_part = fma(rho_d, (double)Lr, -(double)sg);
 
     // pass 3: nu_n(x, j)
     const Rt om1 = (Rt)(1.0 - omega);
-    const Rt oa = (Rt)(omega * alpha), og = (Rt)(omega * gam);
-    const Rt obx = (Rt)(omega * mc.a * bx), oby = (Rt)(omega * mc.a * by),
-             obz = (Rt)(omega * mc.a * bz);
+    const Rt om = (Rt)omega;
+    const Rt oa = om * alpha, og = om * gam;
+    const Rt obx = om * a_r * bx, oby = om * a_r * by, obz = om * a_r * bz;
     nu_out[self] = om1 * lam[0] + oa;
     sfor<0, NP>([&](auto P) {
       constexpr int p = decltype(P)::value;

@@ -201,7 +201,10 @@ bool build_host_model(int model, HostModel* hm) {
     mc.Wf[g] = (float)mc.W[g];
     mc.X2f[g] = (float)mc.X2[g];
   }
-  for (int i = 0; i < vs.Q; ++i) mc.w[i] = hm->w[i];
+  for (int i = 0; i < vs.Q; ++i) {
+    mc.w[i] = hm->w[i];
+    for (int d = 0; d < 3; ++d) mc.e[i][d] = vs.e[i][d];
+  }
   mc.a = a;
   mc.af = (float)a;
   mc.c = hm->c;
@@ -317,6 +320,8 @@ struct lbm_ctx {
   DevBuf mom;         // host-output staging for moments / populations
   DevBuf partials;    // audit block partials
   DevBuf audit_out;   // 8 doubles
+  DevBuf status;      // device int: 1 after a kernel gave up on a bounded wait
+  int variant = 0;    // 0 auto, kVariantDirect, kVariantStaged
   bool inited = false;
   int64_t steps = 0;
   int64_t launches = 0;
@@ -335,10 +340,17 @@ bool all_finite(const double* p, size_t n) {
   return true;
 }
 
+// Default kernel (measured on GB300): the one-cell direct gather for every form.
+int pick_variant(const lbm_ctx* c) {
+  if (c->variant != 0) return c->variant;
+  return kVariantDirect;
+}
+
 int do_steps(lbm_ctx* c, int64_t n) {
+  const int variant = pick_variant(c);
   for (int64_t k = 0; k < n; ++k) {
     cudaError_t e = c->ops->step(c->model, c->state[c->cur].p, c->state[c->cur ^ 1].p, c->g,
-                                 c->omega, c->stream);
+                                 c->omega, variant, static_cast<int*>(c->status.p), c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "stream_collide launch");
     c->cur ^= 1;
     c->launches += 1;
@@ -375,6 +387,8 @@ CtxView ctx_view(lbm_ctx* c) {
   v.steps = &c->steps;
   v.launches = &c->launches;
   v.rec = &c->rec;
+  v.variant = pick_variant(c);
+  v.status = static_cast<int*>(c->status.p);
   return v;
 }
 }  // namespace lbm
@@ -390,6 +404,7 @@ const char* lbm_strerror(int code) {
     case LBM_ECUDA: return "CUDA error";
     case LBM_EUNSTABLE: return "non-finite populations";
     case LBM_ESTATE: return "call out of order";
+    case LBM_EDEVICE: return "device-side timeout";
     default: return "unknown error";
   }
 }
@@ -466,9 +481,17 @@ int lbm_create(lbm_ctx** out, int model, const int64_t dims[3], double omega, in
   if ((rc = c->state[0].ensure(sb, c->stream)) || (rc = c->state[1].ensure(sb, c->stream)) ||
       (rc = c->partials.ensure((size_t)moment_blocks(ncell) * kAuditSlots * sizeof(double),
                                c->stream)) ||
-      (rc = c->audit_out.ensure(kAuditSlots * sizeof(double), c->stream))) {
+      (rc = c->audit_out.ensure(kAuditSlots * sizeof(double), c->stream)) ||
+      (rc = c->status.ensure(sizeof(int), c->stream))) {
     delete c;
     return rc;
+  }
+  {
+    cudaError_t e = cudaMemsetAsync(c->status.p, 0, sizeof(int), c->stream);
+    if (e != cudaSuccess) {
+      delete c;
+      return cuda_fail(e, "status reset");
+    }
   }
   *out = c;
   return LBM_OK;
@@ -487,6 +510,19 @@ int lbm_set_omega(lbm_ctx* c, double omega) {
   if (!(omega >= 0.0 && omega < 2.0)) return fail(LBM_EINVAL, "omega = %g outside [0, 2)", omega);
   c->omega = omega;
   c->rec.valid = false;
+  return LBM_OK;
+}
+
+int lbm_set_variant(lbm_ctx* c, int variant) {
+  if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+  if (variant != 0 && variant != kVariantDirect && variant != kVariantStaged &&
+      variant != kVariantSplit)
+    return fail(LBM_EINVAL, "variant %d", variant);
+  if (variant == kVariantSplit && c->storage == LBM_FP64)
+    return fail(LBM_EINVAL, "the split kernel is for the FP32-arithmetic forms");
+  if (variant == kVariantStaged && !staged_applicable(c->g))
+    return fail(LBM_EINVAL, "the staged kernel needs Nx %% 8 == 0");
+  c->variant = variant;
   return LBM_OK;
 }
 
@@ -661,7 +697,10 @@ int lbm_set_raw(lbm_ctx* c, const void* h, size_t bytes, int where) {
 int lbm_synchronize(lbm_ctx* c) {
   if (!c) return fail(LBM_EINVAL, "ctx is NULL");
   DeviceGuard dg(c->dev);
+  int flag = 0;
+  LBM_CUDA(cudaMemcpyAsync(&flag, c->status.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   LBM_CUDA(cudaStreamSynchronize(c->stream));
+  if (flag) return fail(LBM_EDEVICE, "a staged kernel timed out waiting for its copies");
   return LBM_OK;
 }
 

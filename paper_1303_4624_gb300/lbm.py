@@ -26,7 +26,8 @@ if not os.path.exists(LIB_PATH):
                       "the LBM library has no CPU fallback")
 _lib = ctypes.CDLL(LIB_PATH)
 
-LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ESTATE = 0, -1, -2, -3, -4, -5
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ESTATE, LBM_EDEVICE = 0, -1, -2, -3, -4, -5, -6
+VARIANT_AUTO, VARIANT_DIRECT, VARIANT_STAGED, VARIANT_SPLIT = 0, 1, 2, 3
 LBM_D2Q33, LBM_D3Q95 = 0, 1
 LBM_FP64, LBM_FP32, LBM_FP16DEV, LBM_BF16DEV = 0, 1, 2, 3
 LBM_HOST, LBM_DEVICE = 0, 1
@@ -40,7 +41,7 @@ ADJ_DTYPE = {LBM_FP64: np.float64, LBM_FP32: np.float32, LBM_FP16DEV: np.float32
 
 # exported symbols of include/lbm.h
 SYMBOLS = ("lbm_model_info", "lbm_set_allocator", "lbm_create", "lbm_destroy", "lbm_set_omega",
-           "lbm_set_stream",
+           "lbm_set_variant", "lbm_set_stream",
            "lbm_init", "lbm_step", "lbm_steps_done", "lbm_moments", "lbm_audit",
            "lbm_get_populations", "lbm_set_populations", "lbm_get_raw", "lbm_set_raw",
            "lbm_record", "lbm_backward", "lbm_release_record", "lbm_synchronize",
@@ -56,6 +57,7 @@ _sig = {
     "lbm_create": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(_i64), _d, _i, _vp]),
     "lbm_destroy": (_i, [_vp]),
     "lbm_set_omega": (_i, [_vp, _d]),
+    "lbm_set_variant": (_i, [_vp, _i]),
     "lbm_set_stream": (_i, [_vp, _vp]),
     "lbm_init": (_i, [_vp, _vp, _vp, _vp, _i]),
     "lbm_step": (_i, [_vp, _i64]),
@@ -180,6 +182,10 @@ def lbm_destroy(ctx):
 
 def lbm_set_omega(ctx, omega):
     _check(_lib.lbm_set_omega(ctx, float(omega)), "lbm_set_omega")
+
+
+def lbm_set_variant(ctx, variant):
+    _check(_lib.lbm_set_variant(ctx, int(variant)), "lbm_set_variant")
 
 
 def lbm_set_stream(ctx, stream):

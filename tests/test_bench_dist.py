@@ -1,0 +1,48 @@
+"""The multi-rank path of bench.py on CPU: two gloo ranks, each a replica, time =
+maximum over ranks, units = sum over ranks (the aggregation rank 0 reports)."""
+import os
+import socket
+
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, q):
+    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port),
+                       "RANK": str(rank), "WORLD_SIZE": str(world), "LOCAL_RANK": str(rank)})
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    r, w, local = bench.dist_env()
+    t, u = bench.reduce_max_sum(0.5 + rank, 1000 * (rank + 1))
+    q.put((r, w, local, t, u))
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_aggregate_max_time_and_sum_units():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for r, (rank, world, local, t, u) in enumerate(out):
+        assert rank == r and world == 2 and local == r
+        assert t == pytest.approx(1.5) and u == pytest.approx(3000.0)
+
+
+def test_reduce_is_identity_without_a_process_group():
+    import bench
+    assert bench.reduce_max_sum(0.25, 7) == (0.25, 7)

@@ -1,0 +1,48 @@
+"""Error of the FP32 / FP16 / BF16 storage forms against the FP64 oracle on the
+128 x 32 x 32 run of the precision-sweep setup (D3Q95, omega 1.8, 200 steps,
+(rho, theta) = (1, 1) | (0.5, 0.8), diaphragm at x = 64).
+
+Bars (the benchmark spec): FP32 within 1e-5; FP16 deviation storage rho / T error
+<= 1e-3.  BF16 has 8 significand bits (unit roundoff 2^-9 = 2e-3 on every
+store), so its error is reported, with a bound of 1e-2 that only guards against
+gross failure.  The measured errors are printed (-s) for the record."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import lbm as olbm
+from oracle.model import get_model
+from paper_1303_4624_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+BARS = {"fp32": 1e-5, "fp16": 1e-3, "bf16": 1e-2}
+
+
+@pytest.fixture(scope="module")
+def oracle_fields():
+    wl, fields = W.d3q95_sweep(128, 32, 32)
+    mdl = get_model("D3Q95")
+    S = olbm.init_populations(mdl, fields.rho, fields.U, fields.theta * mdl.T0)
+    S = olbm.run(mdl, S, wl.omega, wl.steps)
+    return wl, fields, olbm.macroscopic(mdl, S)
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
+def test_storage_form_error_vs_fp64_oracle(lbm, oracle_fields, storage):
+    wl, fields, (r0, U0, T0) = oracle_fields
+    lat = lbm.Lattice("D3Q95", wl.dims, wl.omega, storage)
+    lat.init(fields.rho, fields.U, fields.theta * lat.info["T0"])
+    lat.step(wl.steps)
+    rho, U, T = lat.moments()
+    err = {"rho": float(np.max(np.abs(rho - r0) / r0)),
+           "T": float(np.max(np.abs(T - T0) / T0)),
+           "U_over_sqrtT0": float(np.max(np.abs(U - U0)) / np.sqrt(lat.info["T0"]))}
+    print("PRECISION %s %s" % (storage, json.dumps(err)))
+    out = os.environ.get("LBM_PRECISION_LOG")
+    if out:
+        with open(out, "a") as f:
+            f.write(json.dumps({"storage": storage, "grid": "128x32x32", "steps": wl.steps, **err}) + "\n")
+    assert err["rho"] <= BARS[storage] and err["T"] <= BARS[storage], err
