@@ -227,6 +227,30 @@ int lbm_synchronize(lbm_ctx* ctx);
 /* lbm_launch_count - kernels this context has launched so far. */
 int64_t lbm_launch_count(const lbm_ctx* ctx);
 
+/*
+ * lbm_audit_noalloc - the conservation audit of lbm_audit for a caller-owned
+ * population array, allocating no device memory.  The paper has no
+ * counterpart: this exists for callers that cannot call cudaMalloc, such as
+ * code whose device memory belongs in full to another allocator (a framework's
+ * pool that has reserved the GPU) or code in a time loop that cannot take the
+ * device-wide synchronisation cudaMalloc / cudaFree may cause.
+ *   model, storage, dims: as for lbm_create (the layout lbm_get_raw returns);
+ *   h:      device pointer to the stored deviations, Q * cells elements;
+ *   out:    device pointer to 8 doubles, filled as lbm_audit's out (no host copy);
+ *   stream: cudaStream_t the work is ordered on (NULL = legacy default stream).
+ * The per-block partial sums live in one file-scope device array of 8192 x 8
+ * doubles (512 KiB, held by every GPU that loads the library until the process
+ * exits), so grids of at most 2,097,152 cells are accepted; larger grids return
+ * LBM_EINVAL.  The first call on a device does a set-up with that device
+ * current (the array's device address and the constant model tables); make
+ * that first call before any stream capture.  All calls share the array:
+ * calls whose work overlaps on the GPU (other streams, other threads) race.
+ * Each call overwrites every partial it reads, so nothing needs clearing.
+ * Returns after enqueueing.  Errors: LBM_EINVAL, LBM_ECUDA.
+ */
+int lbm_audit_noalloc(int model, int storage, const int64_t dims[3], const void* h, double* out,
+                      void* stream);
+
 /* lbm_strerror - static text for an error code; lbm_last_error - detail of
  * the last failure on the calling thread (empty string if none). */
 const char* lbm_strerror(int code);

@@ -45,7 +45,7 @@ SYMBOLS = ("lbm_model_info", "lbm_set_allocator", "lbm_create", "lbm_destroy", "
            "lbm_init", "lbm_step", "lbm_steps_done", "lbm_moments", "lbm_audit",
            "lbm_get_populations", "lbm_set_populations", "lbm_get_raw", "lbm_set_raw",
            "lbm_record", "lbm_backward", "lbm_release_record", "lbm_synchronize",
-           "lbm_launch_count", "lbm_strerror", "lbm_last_error")
+           "lbm_launch_count", "lbm_audit_noalloc", "lbm_strerror", "lbm_last_error")
 
 _vp, _i, _i64, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -73,6 +73,7 @@ _sig = {
     "lbm_release_record": (_i, [_vp]),
     "lbm_synchronize": (_i, [_vp]),
     "lbm_launch_count": (_i64, [_vp]),
+    "lbm_audit_noalloc": (_i, [_i, _i, ctypes.POINTER(_i64), _vp, _vp, _vp]),
     "lbm_strerror": (ctypes.c_char_p, [_i]),
     "lbm_last_error": (ctypes.c_char_p, []),
 }
@@ -270,6 +271,19 @@ def lbm_synchronize(ctx):
 
 def lbm_launch_count(ctx):
     return int(_lib.lbm_launch_count(ctx))
+
+
+def lbm_audit_noalloc(model, storage, dims, h, out, stream=None):
+    """Audit of a caller-owned device population array into a caller-owned device
+    buffer of 8 doubles, without any device allocation (see include/lbm.h)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    d = (_i64 * 3)(*[int(x) for x in dims])
+    _check(_lib.lbm_audit_noalloc(MODELS.get(model, model), STORAGES.get(storage, storage), d,
+                                  _ptr(h)[0], _ptr(out)[0], stream), "lbm_audit_noalloc")
 
 
 def lbm_strerror(code):
