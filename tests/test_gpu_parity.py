@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
-Tolerances (the benchmark spec): FP64 form 1e-12 relative, FP32 form 1e-5 relative,
+Tolerances (the parity targets): FP64 form 1e-12 relative, FP32 form 1e-5 relative,
 streaming indices bit-exact.  rho and T are compared relative per cell, U
 relative to the sound-speed scale sqrt(T0).  Populations are compared per
 direction, normalised by that direction's largest magnitude; their bound is

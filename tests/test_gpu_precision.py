@@ -2,7 +2,7 @@
 128 x 32 x 32 run of the precision-sweep setup (D3Q95, omega 1.8, 200 steps,
 (rho, theta) = (1, 1) | (0.5, 0.8), diaphragm at x = 64).
 
-Bars (the benchmark spec): FP32 within 1e-5; FP16 deviation storage rho / T error
+Bars (the precision targets): FP32 within 1e-5; FP16 deviation storage rho / T error
 <= 1e-3.  BF16 has 8 significand bits (unit roundoff 2^-9 = 2e-3 on every
 store), so its error is reported, with a bound of 1e-2 that only guards against
 gross failure.  The measured errors are printed (-s) for the record."""
