@@ -51,6 +51,8 @@ def parse_args(argv=None):
     p.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16", "fp64"])
     p.add_argument("--grid", default="128x64x64", help="NXxNYxNZ of the D3Q95 Riemann workload")
     p.add_argument("--no-extras", action="store_true", help="skip the forms / adjoint / cpu legs")
+    p.add_argument("--leg", default=None, choices=["forms", "adjoint", "large"],
+                   help="run one secondary leg alone (for profiling) and print its JSON")
     return p.parse_args(argv)
 
 
@@ -138,9 +140,9 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload_key):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on the
-    current kernel source (its 'source_hash' line matches); else None."""
+def profile_record(workload_key, field):
+    """A number recorded in a committed summary under profiles/, if that summary was
+    taken on the current kernel source (its 'source_hash' line matches); else None."""
     d = os.path.join(ROOT, "profiles")
     if not os.path.isdir(d):
         return None
@@ -152,10 +154,15 @@ def profiled_traffic(workload_key):
             text = f.read()
         m_hash = re.search(r"source_hash:\s*([0-9a-f]+)", text)
         m_key = re.search(r"workload_key:\s*(\S+)", text)
-        m_tr = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
-        if m_hash and m_key and m_tr and m_hash.group(1) == src and m_key.group(1) == workload_key:
-            return float(m_tr.group(1))
+        m_val = re.search(field + r":\s*([0-9.eE+-]+)", text)
+        if m_hash and m_key and m_val and m_hash.group(1) == src and m_key.group(1) == workload_key:
+            return float(m_val.group(1))
     return None
+
+
+def profiled_traffic(workload_key):
+    """DRAM bytes per launch of the stream-collide kernel from the committed ncu summary."""
+    return profile_record(workload_key, "traffic_bytes_per_launch")
 
 
 # ------------------------------------------------------------------ our arm
@@ -196,6 +203,11 @@ def run_ours(args):
     from paper_1303_4624_gb300 import workloads as W
 
     stream = torch.cuda.current_stream()
+    if args.leg:
+        fn = {"forms": forms_leg, "adjoint": adjoint_leg, "large": large_leg}[args.leg]
+        if rank == 0:
+            print(json.dumps({"leg": args.leg, "result": fn(lbm, W, stream)}), flush=True)
+        return
     nx, ny, nz = (int(v) for v in args.grid.lower().split("x"))
     wl, fields = W.d3q95_riemann(nx, ny, nz, storage=args.storage)
     Q = lbm.lbm_model_info(wl.model)["Q"]
@@ -262,6 +274,7 @@ def run_ours(args):
         line["e2e"] = e2e_leg(lbm, W, wl, fields, args.steps, stream)
         line["forms"] = forms_leg(lbm, W, stream)
         line["adjoint"] = adjoint_leg(lbm, W, stream)
+        line["large"] = large_leg(lbm, W, stream)
         line["cpu_baseline"] = cpu_baseline_leg()
     lat.close()
     if rank == 0:
@@ -317,8 +330,73 @@ def forms_leg(lbm, W, stream, steps=200):
         torch.cuda.empty_cache()
     out["fp16_over_fp32"] = round(out["fp16"]["mlups"] / out["fp32"]["mlups"], 3)
     out["bf16_over_fp32"] = round(out["bf16"]["mlups"] / out["fp32"]["mlups"], 3)
-    out["error_vs_fp64_oracle"] = ("measured by tests/test_gpu_precision.py on the 128x32x32 "
-                                   "run of the identical setup (200 steps)")
+    err = {}
+    for st in ("fp32", "fp16", "bf16"):
+        r = profile_record("precision_d3q95_sweep_128x32x32_200", st + "_rho")
+        t = profile_record("precision_d3q95_sweep_128x32x32_200", st + "_T")
+        err[st] = None if r is None else {"rho": r, "T": t}
+    out["error_vs_fp64_oracle"] = err
+    out["error_source"] = ("max relative rho / T error after 200 steps on the 128x32x32 run of "
+                           "the identical setup, from tests/test_gpu_precision.py, recorded in "
+                           "profiles/precision_forms_d3q95_128x32x32.md for this kernel source "
+                           "(null if the kernels changed since)")
+    return out
+
+
+def large_leg(lbm, W, stream, steps=300):
+    """The 768 x 384 x 384 oblique Riemann workload, FP16 deviation storage: the
+    forward, then the adjoint of the final-density MSE (target: the same setup's
+    initial density from seed 2) with the memory-bounded reverse schedule, whose
+    stored-state budget is what fits next to the two FP32 adjoint buffers."""
+    import torch
+    free, _ = torch.cuda.mem_get_info()
+    if free < 60e9:
+        return {"skipped": "needs 60 GB free device memory, %.0f GB free" % (free / 1e9)}
+    wl, fields = W.d3q95_oblique()
+    lat = make_lattice(lbm, wl, fields)
+    dt = time_steps(lbm, lat, steps, 5, stream)
+    a = lat.audit()
+    out = {"workload": wl.name, "storage": "fp16", "steps": steps,
+           "mlups": round(wl.cells * steps / dt / 1e6, 1),
+           "gbs": round(wl.cells * 2 * 95 * 2 / (dt / steps) / 1e9, 1),
+           "nonfinite_after": a["nonfinite"]}
+    # adjoint of L = mean (rho_N - rho*)^2
+    state_b = wl.cells * 95 * 2
+    lam_b = 2 * wl.cells * 95 * 4
+    free, _ = torch.cuda.mem_get_info()
+    budget = int((free - lam_b - 12e9) // state_b)
+    if budget < 2:
+        out["adjoint"] = {"skipped": "%.0f GB free is too little" % (free / 1e9)}
+    else:
+        max_states = min(budget, 12)
+        target = torch.from_numpy(W.d3q95_oblique(seed=2)[1].rho).to("cuda")
+        lat.init(fields.rho, fields.U, fields.theta * lat.info["T0"])
+        del fields
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        lbm.lbm_record_bounded(lat.ctx, steps, max_states)
+        ev[1].record(stream)
+        rhoN = torch.empty_like(target)
+        lbm.lbm_moments(lat.ctx, rhoN, None, None)
+        g = 2.0 * (rhoN - target) / rhoN.numel()
+        loss = float(((rhoN - target) ** 2).mean())
+        d_rho = torch.empty_like(target)
+        torch.cuda.synchronize()
+        ev[2].record(stream)
+        d_om = lbm.lbm_backward(lat.ctx, g, d_rho, None, None)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        fw = ev[0].elapsed_time(ev[1]) / 1e3
+        bw = ev[2].elapsed_time(ev[3]) / 1e3
+        out["adjoint"] = {"loss": loss, "dL_domega": d_om,
+                          "dL_drho0_rms": float(d_rho.pow(2).mean().sqrt()),
+                          "max_states": max_states, "forward_s": round(fw, 3),
+                          "backward_s": round(bw, 3), "backward_over_forward": round(bw / fw, 2),
+                          "schedule": "bisection over %d stored FP16 states" % max_states}
+        del target, rhoN, g, d_rho
+    lbm.lbm_release_record(lat.ctx)
+    lat.close()
+    torch.cuda.empty_cache()
     return out
 
 

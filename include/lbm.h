@@ -201,6 +201,20 @@ int lbm_set_raw(lbm_ctx* ctx, const void* h, size_t bytes, int where);
 int lbm_record(lbm_ctx* ctx, int64_t nsteps, int64_t ckpt_every);
 
 /*
+ * lbm_record_bounded - the same forward as lbm_record, for grids whose uniform
+ * checkpoints do not fit: only S_0 is kept.  The reverse sweep of lbm_backward
+ * then stores at most max_states >= 1 states (S_0 included), placed by recursive
+ * bisection of the step range; ranges deeper than the budget are recomputed
+ * from their nearest stored state.  Recomputation is about (log2(nsteps) / 2 +
+ * nsteps / 2^max_states) sweeps; e.g. 6 states for 300 steps cost ~4 forward
+ * sweeps.  The context's two population buffers serve as work space: after such
+ * a backward the context holds S_0 (steps done = 0).  Gradients are bitwise
+ * identical to the uniform schedule's.
+ * Errors: LBM_ESTATE (no lbm_init), LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA.
+ */
+int lbm_record_bounded(lbm_ctx* ctx, int64_t nsteps, int64_t max_states);
+
+/*
  * lbm_backward - reverse sweep of the recorded rollout: the exact discrete
  * adjoint of the stream-collide update (transposed collision Jacobian through
  * f^eq, then reverse streaming), recomputing each segment of ckpt_every

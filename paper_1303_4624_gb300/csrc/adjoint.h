@@ -33,6 +33,9 @@ struct Record {
   int64_t nsteps = 0;
   int64_t k = 0;
   int final_buf = 0;                            // state buffer holding S_N
+  bool tail_kept = false;                       // seg[] holds the last segment's states
+  bool bounded = false;                         // lbm_record_bounded: bisection schedule
+  int64_t max_states = 0;                       // stored-state budget of the bounded schedule
   std::vector<std::unique_ptr<DevBuf>> ckpt;    // ceil(nsteps / k) states
   std::vector<std::unique_ptr<DevBuf>> seg;     // k - 1 replayed states
   DevBuf nu[2];                                 // adjoint ping-pong, Q * cells of the adjoint type

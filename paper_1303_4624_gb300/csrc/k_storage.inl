@@ -4,6 +4,7 @@
 #include <mutex>
 
 #include "kernels.cuh"
+#include "adjoint_kernels.cuh"
 
 namespace lbm {
 namespace {

@@ -863,313 +863,3 @@ __global__ void k_set_f(const double* __restrict__ f, S* __restrict__ dst, Grid 
 }
 
 }  // namespace lbm
-
-namespace lbm {
-
-// ----------------------------------------------------------------- adjoint
-// Discrete adjoint of one pull stream-collide step (exact transpose, arithmetic
-// type L = FP32 or FP64).  Variables are derivatives with respect to the
-// physical populations f.  With nu_n(x, j) = dL/dg^(n)_j(x) for the populations
-// gathered by step n and lambda_{n+1}(x, i) = dL/dS_{n+1}(x, i) = nu_{n+1}(x + e_i, i):
-//   nu_n(x, j) = (1 - omega) lambda_j + omega (alpha + beta . xi_j + gamma |xi_j|^2)
-// because f^eq depends on g only through M = (rho, j, E) with dM/dg_j = (1, xi_j, |xi_j|^2)
-// (the collision Jacobian has rank D + 2 beyond its diagonal).  alpha, beta,
-// gamma = sum_i lambda_i d f_i^eq / dM, through f_i^eq = w_i rho P(s_i; q, t):
-//   dP/ds = A1 + 2 A2 s + s^2/2 + s^3/6
-//   dP/dq = Bq - s/2 - s^2/4,            Bq = -1/2 + q/4 + t (D+2-x2)/4
-//   dP/dt = Bt + Ct s + Dt s^2,          Bt = (x2-D)/2 + (D+2-x2) q/4 + t (x2^2 - 2(D+2) x2 + D(D+2))/4
-//                                        Ct = (x2-D-2)/2, Dt = (x2-D-4)/4
-// and the chain rule from (rho, u, theta) to M:
-//   d u/d rho = -u/rho, d u/d j = 1/rho, d theta/d rho = (q - D theta)/(D rho),
-//   d theta/d j = -2 u/(D rho), d theta/d E = 1/(D rho).
-// dL/domega of the step is sum_i lambda_i (f_i^eq - g_i) = rho Lrho - sum_i lambda_i w_i (1 + h_i).
-template <class R, int D>
-struct EqGrad {
-  R q, t;
-  __device__ __forceinline__ EqGrad(R q_, R t_) : q(q_), t(t_) {}
-  __device__ __forceinline__ R Bq(R x2) const {
-    return R(-0.5) + q * R(0.25) + t * (R(D + 2) - x2) * R(0.25);
-  }
-  __device__ __forceinline__ R Bt(R x2) const {
-    return (x2 - R(D)) * R(0.5) + (R(D + 2) - x2) * q * R(0.25) +
-           t * (x2 * x2 - R(2 * (D + 2)) * x2 + R(D * (D + 2))) * R(0.25);
-  }
-  static __device__ __forceinline__ R Ct(R x2) { return (x2 - R(D + 2)) * R(0.5); }
-  static __device__ __forceinline__ R Dt(R x2) { return (x2 - R(D + 4)) * R(0.25); }
-};
-
-template <class R>
-__device__ __forceinline__ void comp_add(R& s, R& c, R x) {
-  if constexpr (std::is_same<R, float>::value) kahan_add(s, c, x); else s += x;
-}
-
-__device__ __forceinline__ double block_sum_128(double v, double* sh) {
-  v = warp_sum(v);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) sh[wid] = v;
-  __syncthreads();
-  double r = 0;
-  if (threadIdx.x == 0)
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += sh[w];
-  return r;
-}
-
-#ifndef LBM_ADJ_MINB
-#define LBM_ADJ_MINB 2
-#endif
-template <class S>
-struct AdjMinBlocks {
-  static constexpr int value = std::is_same<S, double>::value ? 1 : LBM_ADJ_MINB;
-};
-template <int M, class S, class L, bool kFirst>
-__global__ void __launch_bounds__(128, AdjMinBlocks<S>::value)
-    k_adjoint(const S* __restrict__ state, const L* __restrict__ nu_next,
-              const double* __restrict__ dldrho, L* __restrict__ nu_out,
-              double* __restrict__ omega_acc, Grid g, double omega) {
-  using Mo = Model<M>;
-  using Rt = L;
-  constexpr int Q = Mo::Q, D = Mo::D, RR = Mo::R, NP = Mo::NP;
-  const ModelConst& mc = c_mc[M];
-  __shared__ double sh[4];
-
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y, z = blockIdx.z;
-  const bool active = x < g.nx;
-  double om_part = 0.0;
-  if (active) {
-    int xo[2 * RR + 1], yo[2 * RR + 1], zo[2 * RR + 1];
-    sfor<0, 2 * RR + 1>([&](auto K) {
-      constexpr int k = decltype(K)::value;
-      xo[k] = wrapi(x - (k - RR), g.nx);
-      yo[k] = wrapi(y - (k - RR), g.ny) * g.nx;
-      if constexpr (D == 3) zo[k] = wrapi(z - (k - RR), g.nz) * g.nxy; else zo[k] = 0;
-    });
-    const size_t self = ((size_t)z * g.ny + y) * g.nx + x;
-    Rt lam[Q];
-    Rt l1 = Rt(0);
-    if constexpr (kFirst) l1 = (Rt)dldrho[self];
-    // pass 1: lambda (gathered from x + e_i), forward moments of g (gathered from x - e_i)
-    Rt rs, rc = Rt(0), es = Rt(0), ec = Rt(0), jx = Rt(0), jy = Rt(0), jz = Rt(0), sg;
-    {
-      const Rt h0 = (Rt)Codec<S>::ld(state + self);
-      lam[0] = kFirst ? l1 : nu_next[self];
-      rs = gW<Rt>(mc, 0) * h0;
-      sg = gW<Rt>(mc, 0) * lam[0] * (Rt(1) + h0);
-    }
-    sfor<0, NP>([&](auto P) {
-      constexpr int p = decltype(P)::value;
-      constexpr int ip = 1 + 2 * p, im = 2 + 2 * p;
-      constexpr int gg = Mo::vs.grp[ip];
-      constexpr int ex = Mo::vs.e[ip][0], ey = Mo::vs.e[ip][1], ez = Mo::vs.e[ip][2];
-      const int cm = zo[ez + RR] + yo[ey + RR] + xo[ex + RR];   // x - e_ip
-      const int cp = zo[RR - ez] + yo[RR - ey] + xo[RR - ex];   // x + e_ip
-      const Rt hp = (Rt)Codec<S>::ld(state + (size_t)ip * g.ncell + cm);
-      const Rt hm = (Rt)Codec<S>::ld(state + (size_t)im * g.ncell + cp);
-      if constexpr (kFirst) {
-        lam[ip] = l1;
-        lam[im] = l1;
-      } else {
-        lam[ip] = nu_next[(size_t)ip * g.ncell + cp];
-        lam[im] = nu_next[(size_t)im * g.ncell + cm];
-      }
-      const Rt w = gW<Rt>(mc, gg);
-      const Rt tr = w * (hp + hm);
-      comp_add(rs, rc, tr);
-      comp_add(es, ec, gX2<Rt>(mc, gg) * tr);
-      const Rt tj = w * (hp - hm);
-      if constexpr (ex != 0) jx += Rt(ex) * tj;
-      if constexpr (ey != 0) jy += Rt(ey) * tj;
-      if constexpr (ez != 0) jz += Rt(ez) * tj;
-      sg += w * (lam[ip] * (Rt(1) + hp) + lam[im] * (Rt(1) + hm));
-    });
-    // forward moments and temperature, as in the forward step (FP64 only for theta - 1)
-    Rt q, t, ux, uy, uz, rho_r, ir_r;
-    double rho_d;
-    if constexpr (std::is_same<Rt, float>::value) {
-      rho_r = 1.0f + (rs - rc);
-      ir_r = __fdividef(1.0f, rho_r);
-      ux = mc.af * jx * ir_r;
-      uy = mc.af * jy * ir_r;
-      uz = (D == 3) ? mc.af * jz * ir_r : 0.0f;
-      q = ux * ux + uy * uy + uz * uz;
-      const double rd = (double)rs - (double)rc;
-      const double ed = (double)es - (double)ec;
-      rho_d = 1.0 + rd;
-      double ir = (double)ir_r;
-      ir = fma(ir, fma(-rho_d, ir, 1.0), ir);
-      t = (float)(fma(fma(-(double)D, rd, ed), ir, -(double)q) * (1.0 / D));
-    } else {
-      rho_d = 1.0 + rs;
-      rho_r = rho_d;
-      ir_r = 1.0 / rho_d;
-      ux = mc.a * jx * ir_r;
-      uy = mc.a * jy * ir_r;
-      uz = (D == 3) ? mc.a * jz * ir_r : 0.0;
-      q = ux * ux + uy * uy + uz * uz;
-      t = ((es - (double)D * rs) * ir_r - q) * (1.0 / D);
-    }
-    const Rt theta = Rt(1) + t;
-    const EqCoef<Rt, D> cf(q, t);
-    const EqGrad<Rt, D> gr(q, t);
-    const Rt a_r = gA<Rt>(mc);
-    const Rt uax = a_r * ux, uay = a_r * uy, uaz = a_r * uz;
-
-    // pass 2: contractions with lambda
-    Rt Lr = gW<Rt>(mc, 0) * lam[0] * cf.K0;
-    Rt Sq = gW<Rt>(mc, 0) * lam[0] * gr.Bq(Rt(0));
-    Rt St = gW<Rt>(mc, 0) * lam[0] * gr.Bt(Rt(0));
-    Rt Vx = Rt(0), Vy = Rt(0), Vz = Rt(0);
-    sfor<0, NP>([&](auto P) {
-      constexpr int p = decltype(P)::value;
-      constexpr int ip = 1 + 2 * p, im = 2 + 2 * p;
-      constexpr int gg = Mo::vs.grp[ip];
-      constexpr int ex = Mo::vs.e[ip][0], ey = Mo::vs.e[ip][1], ez = Mo::vs.e[ip][2];
-      const Rt x2 = gX2<Rt>(mc, gg);
-      const Rt w = gW<Rt>(mc, gg);
-      Rt s = Rt(0);
-      if constexpr (ex != 0) s += Rt(ex) * uax;
-      if constexpr (ey != 0) s += Rt(ey) * uay;
-      if constexpr (ez != 0) s += Rt(ez) * uaz;
-      const Rt s2 = s * s;
-      const Rt A1 = cf.A1(x2), A2 = cf.A2(x2);
-      const Rt Pe = cf.A0(x2) + s2 * (A2 + s2 * Rt(1.0 / 24.0));
-      const Rt Po = s * (A1 + s2 * Rt(1.0 / 6.0));
-      const Rt Pse = A1 + s2 * Rt(0.5);
-      const Rt Pso = s * (Rt(2) * A2 + s2 * Rt(1.0 / 6.0));
-      const Rt Pqe = gr.Bq(x2) - s2 * Rt(0.25);
-      const Rt Pqo = s * Rt(-0.5);
-      const Rt Pte = gr.Bt(x2) + EqGrad<Rt, D>::Dt(x2) * s2;
-      const Rt Pto = EqGrad<Rt, D>::Ct(x2) * s;
-      const Rt ls = lam[ip] + lam[im], ld = lam[ip] - lam[im];
-      Lr += w * (ls * Pe + ld * Po);
-      Sq += w * (ls * Pqe + ld * Pqo);
-      St += w * (ls * Pte + ld * Pto);
-      const Rt v = w * (ld * Pse + ls * Pso);
-      if constexpr (ex != 0) Vx += Rt(ex) * v;
-      if constexpr (ey != 0) Vy += Rt(ey) * v;
-      if constexpr (ez != 0) Vz += Rt(ez) * v;
-    });
-    // chain rule to the moments (arithmetic type; the omega term in FP64)
-    const Rt Lux = rho_r * (a_r * Vx + Rt(2) * ux * Sq);
-    const Rt Luy = rho_r * (a_r * Vy + Rt(2) * uy * Sq);
-    const Rt Luz = (D == 3) ? rho_r * (a_r * Vz + Rt(2) * uz * Sq) : Rt(0);
-    const Rt Lt = rho_r * St;
-    const Rt iDr = ir_r * Rt(1.0 / D);
-    const Rt alpha = Lr - (ux * Lux + uy * Luy + uz * Luz) * ir_r + Lt * (q - Rt(D) * theta) * iDr;
-    const Rt bx = Lux * ir_r - Rt(2) * Lt * ux * iDr;
-    const Rt by = Luy * ir_r - Rt(2) * Lt * uy * iDr;
-    const Rt bz = Luz * ir_r - Rt(2) * Lt * uz * iDr;
-    const Rt gam = Lt * iDr;
-    om_part = fma(rho_d, (double)Lr, -(double)sg);
-
-    // pass 3: nu_n(x, j)
-    const Rt om1 = (Rt)(1.0 - omega);
-    const Rt om = (Rt)omega;
-    const Rt oa = om * alpha, og = om * gam;
-    const Rt obx = om * a_r * bx, oby = om * a_r * by, obz = om * a_r * bz;
-    nu_out[self] = om1 * lam[0] + oa;
-    sfor<0, NP>([&](auto P) {
-      constexpr int p = decltype(P)::value;
-      constexpr int ip = 1 + 2 * p, im = 2 + 2 * p;
-      constexpr int gg = Mo::vs.grp[ip];
-      constexpr int ex = Mo::vs.e[ip][0], ey = Mo::vs.e[ip][1], ez = Mo::vs.e[ip][2];
-      const Rt ev = oa + og * gX2<Rt>(mc, gg);
-      Rt od = Rt(0);
-      if constexpr (ex != 0) od += Rt(ex) * obx;
-      if constexpr (ey != 0) od += Rt(ey) * oby;
-      if constexpr (ez != 0) od += Rt(ez) * obz;
-      nu_out[(size_t)ip * g.ncell + self] = om1 * lam[ip] + (ev + od);
-      nu_out[(size_t)im * g.ncell + self] = om1 * lam[im] + (ev - od);
-    });
-  }
-  const double bsum = block_sum_128(om_part, sh);
-  if (threadIdx.x == 0) {
-    const size_t b = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    omega_acc[b] += bsum;
-  }
-}
-
-// dL/d(rho0, U0, T0): lambda_0(x, i) = nu0(x + e_i, i) contracted with the
-// derivatives of f_i^eq(rho, u, theta) at the initial fields (FP64).
-template <int M, class L>
-__global__ void __launch_bounds__(128)
-    k_grad_init(const L* __restrict__ nu0, const double* __restrict__ fields,
-                double* __restrict__ d_rho, double* __restrict__ d_U, double* __restrict__ d_T,
-                Grid g) {
-  using Mo = Model<M>;
-  constexpr int D = Mo::D, RR = Mo::R, NP = Mo::NP;
-  const ModelConst& mc = c_mc[M];
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= g.nx) return;
-  const int y = blockIdx.y, z = blockIdx.z;
-  int xo[2 * RR + 1], yo[2 * RR + 1], zo[2 * RR + 1];
-  sfor<0, 2 * RR + 1>([&](auto K) {
-    constexpr int k = decltype(K)::value;
-    xo[k] = wrapi(x - (k - RR), g.nx);
-    yo[k] = wrapi(y - (k - RR), g.ny) * g.nx;
-    if constexpr (D == 3) zo[k] = wrapi(z - (k - RR), g.nz) * g.nxy; else zo[k] = 0;
-  });
-  const size_t self = ((size_t)z * g.ny + y) * g.nx + x;
-  const size_t n = (size_t)g.ncell;
-  const double rho = fields[self];
-  const double ux = mc.a * fields[n + self], uy = mc.a * fields[2 * n + self];
-  const double uz = (D == 3) ? mc.a * fields[3 * n + self] : 0.0;
-  const double theta = fields[(size_t)(D + 1) * n + self] / mc.T0;
-  const double q = ux * ux + uy * uy + uz * uz, t = theta - 1.0;
-  const EqCoef<double, D> cf(q, t);
-  const EqGrad<double, D> gr(q, t);
-  const double uax = mc.a * ux, uay = mc.a * uy, uaz = mc.a * uz;
-  const double l0 = (double)nu0[self];
-  double Lr = mc.W[0] * l0 * cf.K0, Sq = mc.W[0] * l0 * gr.Bq(0.0), St = mc.W[0] * l0 * gr.Bt(0.0);
-  double Vx = 0, Vy = 0, Vz = 0;
-  sfor<0, NP>([&](auto P) {
-    constexpr int p = decltype(P)::value;
-    constexpr int ip = 1 + 2 * p, im = 2 + 2 * p;
-    constexpr int gg = Mo::vs.grp[ip];
-    constexpr int ex = Mo::vs.e[ip][0], ey = Mo::vs.e[ip][1], ez = Mo::vs.e[ip][2];
-    const int cm = zo[ez + RR] + yo[ey + RR] + xo[ex + RR];
-    const int cp = zo[RR - ez] + yo[RR - ey] + xo[RR - ex];
-    const double lp = (double)nu0[(size_t)ip * n + cp];
-    const double lm = (double)nu0[(size_t)im * n + cm];
-    const double x2 = mc.X2[gg], w = mc.W[gg];
-    const double s = ex * uax + ey * uay + ez * uaz, s2 = s * s;
-    const double A1 = cf.A1(x2), A2 = cf.A2(x2);
-    const double Pe = cf.A0(x2) + s2 * (A2 + s2 / 24.0), Po = s * (A1 + s2 / 6.0);
-    const double Pse = A1 + 0.5 * s2, Pso = s * (2.0 * A2 + s2 / 6.0);
-    const double Pqe = gr.Bq(x2) - 0.25 * s2, Pqo = -0.5 * s;
-    const double Pte = gr.Bt(x2) + EqGrad<double, D>::Dt(x2) * s2, Pto = EqGrad<double, D>::Ct(x2) * s;
-    const double ls = lp + lm, ld = lp - lm;
-    Lr += w * (ls * Pe + ld * Po);
-    Sq += w * (ls * Pqe + ld * Pqo);
-    St += w * (ls * Pte + ld * Pto);
-    const double v = w * (ld * Pse + ls * Pso);
-    Vx += ex * v;
-    Vy += ey * v;
-    Vz += ez * v;
-  });
-  if (d_rho) d_rho[self] = Lr;
-  if (d_U) {
-    d_U[self] = mc.a * rho * (mc.a * Vx + 2.0 * ux * Sq);
-    d_U[n + self] = mc.a * rho * (mc.a * Vy + 2.0 * uy * Sq);
-    if (D == 3) d_U[2 * n + self] = mc.a * rho * (mc.a * Vz + 2.0 * uz * Sq);
-  }
-  if (d_T) d_T[self] = rho * St / mc.T0;
-}
-
-// Fixed-order sum of n FP64 partials by one block of 256 threads.
-static __global__ void __launch_bounds__(256) k_sum_reduce(const double* __restrict__ partials,
-                                                           long long n, double* __restrict__ out) {
-  double acc = 0;
-  for (long long b = threadIdx.x; b < n; b += blockDim.x) acc += partials[b];
-  __shared__ double sh[8];
-  acc = warp_sum(acc);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double v = 0;
-    for (int w = 0; w < 8; ++w) v += sh[w];
-    *out = v;
-  }
-}
-
-}  // namespace lbm

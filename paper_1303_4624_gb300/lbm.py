@@ -44,7 +44,7 @@ SYMBOLS = ("lbm_model_info", "lbm_set_allocator", "lbm_create", "lbm_destroy", "
            "lbm_set_variant", "lbm_set_stream",
            "lbm_init", "lbm_step", "lbm_steps_done", "lbm_moments", "lbm_audit",
            "lbm_get_populations", "lbm_set_populations", "lbm_get_raw", "lbm_set_raw",
-           "lbm_record", "lbm_backward", "lbm_release_record", "lbm_synchronize",
+           "lbm_record", "lbm_record_bounded", "lbm_backward", "lbm_release_record", "lbm_synchronize",
            "lbm_launch_count", "lbm_audit_noalloc", "lbm_strerror", "lbm_last_error")
 
 _vp, _i, _i64, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
@@ -69,6 +69,7 @@ _sig = {
     "lbm_get_raw": (_i, [_vp, _vp, ctypes.c_size_t, _i]),
     "lbm_set_raw": (_i, [_vp, _vp, ctypes.c_size_t, _i]),
     "lbm_record": (_i, [_vp, _i64, _i64]),
+    "lbm_record_bounded": (_i, [_vp, _i64, _i64]),
     "lbm_backward": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i]),
     "lbm_release_record": (_i, [_vp]),
     "lbm_synchronize": (_i, [_vp]),
@@ -250,6 +251,10 @@ def lbm_set_raw(ctx, h):
 
 def lbm_record(ctx, nsteps, ckpt_every):
     _check(_lib.lbm_record(ctx, int(nsteps), int(ckpt_every)), "lbm_record")
+
+
+def lbm_record_bounded(ctx, nsteps, max_states):
+    _check(_lib.lbm_record_bounded(ctx, int(nsteps), int(max_states)), "lbm_record_bounded")
 
 
 def lbm_backward(ctx, dL_drhoN, dL_drho0=None, dL_dU0=None, dL_dT0=None):
