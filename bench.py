@@ -424,8 +424,14 @@ def adjoint_leg(lbm, W, stream, n=128, steps=500, k=22):
     lbm.lbm_release_record(lat.ctx)
     lat.close()
     torch.cuda.empty_cache()
+    # the backward replays every segment but the last (kept by the record) once
+    replay = steps - (steps + k - 1) // k - (min(k, steps) - 1)
+    t_step = fwd / steps
+    adj_per_step = (bwd - replay * t_step) / steps
     return {"workload": wl.name, "steps": steps, "ckpt_every": k, "forward_s": round(fwd, 4),
             "backward_s": round(bwd, 4), "backward_over_forward": round(bwd / fwd, 3),
+            "replayed_steps": replay,
+            "adjoint_step_over_forward_step": round(adj_per_step / t_step, 3),
             "forward_mlups": round(wl.cells * steps / fwd / 1e6, 1)}
 
 

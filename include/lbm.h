@@ -132,6 +132,20 @@ int lbm_set_omega(lbm_ctx* ctx, double omega);
  */
 int lbm_set_variant(lbm_ctx* ctx, int variant);
 
+/*
+ * lbm_set_fixed_ends - the end conditions of the paper's shock tube (paragraph
+ * before Figure 1: the left and right boundary planes carry the fixed states C_L
+ * and C_R).  After every later lbm_step the first and the last `width` planes
+ * along `axis` (0 x, 1 y, 2 z) are set to the discrete equilibrium of state `lo`
+ * and `hi`; the other axes stay periodic.  States are {rho, U_1..U_D, T} in
+ * lattice units (host arrays of D + 2 doubles).  width must be at least the
+ * stencil reach (4 for D2Q33, 5 for D3Q95), so that no other cell gathers across
+ * the ends, and at most N/2; width 0 switches the ends off.  Not covered by the
+ * adjoint: lbm_record / lbm_record_bounded return LBM_EINVAL while active.
+ * Errors: LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA.
+ */
+int lbm_set_fixed_ends(lbm_ctx* ctx, int axis, int width, const double* lo, const double* hi);
+
 /* lbm_set_stream - order later calls on another stream of the same device. */
 int lbm_set_stream(lbm_ctx* ctx, void* stream);
 

@@ -90,9 +90,35 @@ def step(model, S, omega):
     return collide(model, stream(model, S), omega)
 
 
-def run(model, S, omega, nsteps):
+def run(model, S, omega, nsteps, ends=None):
+    """nsteps steps; ``ends`` = (axis, width, (rho, U, T)_lo, (rho, U, T)_hi) holds
+    the first and last ``width`` planes along ``axis`` at the discrete equilibrium
+    of the two states after every step (see fixed_ends)."""
     for _ in range(nsteps):
         S = step(model, S, omega)
+        if ends is not None:
+            S = fixed_ends(model, S, *ends)
+    return S
+
+
+def fixed_ends(model, S, axis, width, lo, hi):
+    """The shock tube's end conditions (paragraph before Figure 1): the planes
+    with coordinate < width along ``axis`` take f^eq of state ``lo``, those with
+    coordinate >= N - width take f^eq of ``hi``.  States are (rho, U [D], T) in
+    lattice units; axis 0, 1, 2 = x, y, z.  width >= the stencil reach keeps every
+    other cell's gathers inside the tube (no wrap through the ends)."""
+    S = S.copy()
+    arr_axis = 3 - axis                      # S is [Q, z, y, x]
+    n = S.shape[arr_axis]
+    for state, sl in ((lo, slice(0, width)), (hi, slice(n - width, n))):
+        rho, U, T = state
+        u, theta = to_xi_units(model, np.asarray(U, dtype=np.float64).reshape(model.D, 1),
+                               np.array([T], dtype=np.float64))
+        fe = feq(model, np.array([float(rho)]), u, theta)[:, 0]
+        idx = [slice(None)] * 4
+        idx[arr_axis] = sl
+        shape = [model.Q, 1, 1, 1]
+        S[tuple(idx)] = fe.reshape(shape)
     return S
 
 

@@ -60,6 +60,7 @@ struct CtxView {
   Record* rec;
   int variant;      // stream-collide kernel variant the context uses
   int* status;      // device status flag
+  bool fixed_ends;  // fixed-state end planes active (no adjoint for them)
 };
 
 int ctx_fail(int code, const char* msg);

@@ -45,6 +45,10 @@ struct StorageOps {
                          double* T, double* partials, cudaStream_t st);
   cudaError_t (*get_f)(int model, const void* src, double* f, const Grid& g, cudaStream_t st);
   cudaError_t (*set_f)(int model, const double* f, void* dst, const Grid& g, cudaStream_t st);
+  // Overwrite the first / last `width` planes along `axis` (0 x, 1 y, 2 z) with the
+  // populations of template cell 0 / 1 (tmpl is [Q][2] in the storage type).
+  cudaError_t (*fix_ends)(void* state, const Grid& g, int axis, int width, const void* tmpl, int Q,
+                          cudaStream_t st);
   // Adjoint (lambda type: FP64 for the FP64 form, FP32 otherwise).
   int adj_elem_bytes;
   // One reverse step: nu_out = (collision Jacobian)^T lambda_{n+1} with

@@ -162,6 +162,13 @@ cudaError_t grad_init(int m, const void* nu0, const double* fields, double* d_rh
                 : grad_init_m<1>(nu0, fields, d_rho, d_U, d_T, g, st);
 }
 
+cudaError_t fix_ends(void* state, const Grid& g, int axis, int width, const void* tmpl, int Q,
+                     cudaStream_t st) {
+  k_fix_ends<S><<<256, 256, 0, st>>>(static_cast<S*>(state), g, axis, width,
+                                     static_cast<const S*>(tmpl), Q);
+  return cudaGetLastError();
+}
+
 cudaError_t init(int m, const double* rho, const double* U, const double* T, void* dst,
                  const Grid& g, cudaStream_t st) {
   return m == 0 ? init_m<0>(rho, U, T, dst, g, st) : init_m<1>(rho, U, T, dst, g, st);
@@ -185,8 +192,8 @@ cudaError_t set_f(int m, const double* f, void* dst, const Grid& g, cudaStream_t
 
 }  // namespace
 
-const StorageOps LBM_OPS = {(int)sizeof(S), upload, init,          step,
-                            moments,        get_f,  set_f,         (int)sizeof(L),
-                            adjoint_step,   grad_init};
+const StorageOps LBM_OPS = {(int)sizeof(S), upload,       init,      step,
+                            moments,        get_f,        set_f,     fix_ends,
+                            (int)sizeof(L), adjoint_step, grad_init};
 
 }  // namespace lbm

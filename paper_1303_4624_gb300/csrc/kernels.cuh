@@ -862,4 +862,33 @@ __global__ void k_set_f(const double* __restrict__ f, S* __restrict__ dst, Grid 
   }
 }
 
+// ----------------------------------------------------------------- fixed end planes
+// The shock tube's end conditions: after a step, the cells with coordinate
+// < width (side 0) or >= N - width (side 1) along `axis` take the populations of
+// template cell `side` (the discrete equilibrium of that side's state).
+template <class S>
+__global__ void k_fix_ends(S* __restrict__ state, Grid g, int axis, int width,
+                           const S* __restrict__ tmpl, int Q) {
+  const int n_ax = axis == 0 ? g.nx : (axis == 1 ? g.ny : g.nz);
+  const long long per_layer = g.ncell / n_ax;
+  const long long total = 2LL * width * per_layer;
+  for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < total;
+       b += (long long)gridDim.x * blockDim.x) {
+    const long long layer = b / per_layer;            // 0 .. 2 width - 1
+    const long long r = b - layer * per_layer;        // position within the plane
+    const int side = layer < width ? 0 : 1;
+    const int c_ax = side == 0 ? (int)layer : n_ax - 2 * width + (int)layer;
+    long long cell;
+    if (axis == 2) {
+      cell = (long long)c_ax * g.nxy + r;
+    } else if (axis == 1) {
+      const long long z = r / g.nx, x = r - z * g.nx;
+      cell = (z * g.ny + c_ax) * g.nx + x;
+    } else {
+      cell = r * g.nx + c_ax;                        // r runs over (z, y) rows
+    }
+    for (int i = 0; i < Q; ++i) state[(size_t)i * g.ncell + cell] = tmpl[2 * i + side];
+  }
+}
+
 }  // namespace lbm

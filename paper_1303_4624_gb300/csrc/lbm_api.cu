@@ -322,6 +322,8 @@ struct lbm_ctx {
   DevBuf audit_out;   // 8 doubles
   DevBuf status;      // device int: 1 after a kernel gave up on a bounded wait
   int variant = 0;    // 0 auto, kVariantDirect, kVariantStaged
+  int fix_axis = 0, fix_width = 0;   // fixed-state end planes (width 0: none)
+  DevBuf fix_tmpl;    // [Q][2] populations of the two end states
   bool inited = false;
   int64_t steps = 0;
   int64_t launches = 0;
@@ -354,6 +356,12 @@ int do_steps(lbm_ctx* c, int64_t n) {
     if (e != cudaSuccess) return cuda_fail(e, "stream_collide launch");
     c->cur ^= 1;
     c->launches += 1;
+    if (c->fix_width > 0) {
+      e = c->ops->fix_ends(c->state[c->cur].p, c->g, c->fix_axis, c->fix_width, c->fix_tmpl.p, c->Q,
+                           c->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "fix_ends launch");
+      c->launches += 1;
+    }
   }
   c->steps += n;
   return LBM_OK;
@@ -388,6 +396,7 @@ CtxView ctx_view(lbm_ctx* c) {
   v.launches = &c->launches;
   v.rec = &c->rec;
   v.variant = pick_variant(c);
+  v.fixed_ends = c->fix_width > 0;
   v.status = static_cast<int*>(c->status.p);
   return v;
 }
@@ -523,6 +532,49 @@ int lbm_set_variant(lbm_ctx* c, int variant) {
   if (variant == kVariantStaged && !staged_applicable(c->g))
     return fail(LBM_EINVAL, "the staged kernel needs Nx %% 8 == 0");
   c->variant = variant;
+  return LBM_OK;
+}
+
+int lbm_set_fixed_ends(lbm_ctx* c, int axis, int width, const double* lo, const double* hi) {
+  if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+  if (width == 0) {
+    c->fix_width = 0;
+    return LBM_OK;
+  }
+  if (axis < 0 || axis >= c->D) return fail(LBM_EINVAL, "axis %d", axis);
+  const int R = c->model == LBM_D2Q33 ? Model<0>::R : Model<1>::R;
+  const int n_ax = axis == 0 ? c->g.nx : (axis == 1 ? c->g.ny : c->g.nz);
+  if (width < R || 2 * width > n_ax)
+    return fail(LBM_EINVAL, "width %d: need reach (%d) <= width <= N/2 (%d)", width, R, n_ax / 2);
+  if (!lo || !hi) return fail(LBM_EINVAL, "end states are required");
+  const int D = c->D;
+  double host[2 * 5];   // rho[2] | U[D][2] | T[2]
+  for (int s = 0; s < 2; ++s) {
+    const double* st = s == 0 ? lo : hi;
+    for (int k = 0; k < D + 2; ++k)
+      if (!std::isfinite(st[k])) return fail(LBM_EINVAL, "end state has non-finite values");
+    if (!(st[0] > 0.0 && st[D + 1] > 0.0)) return fail(LBM_EINVAL, "end state needs rho > 0, T > 0");
+    host[s] = st[0];
+    for (int d = 0; d < D; ++d) host[2 + 2 * d + s] = st[1 + d];
+    host[2 + 2 * D + s] = st[D + 1];
+  }
+  DeviceGuard dg(c->dev);
+  DevBuf fields;
+  int rc;
+  if ((rc = fields.ensure(sizeof host, c->stream)) ||
+      (rc = c->fix_tmpl.ensure((size_t)c->Q * 2 * c->ops->elem_bytes, c->stream)))
+    return rc;
+  LBM_CUDA(cudaMemcpyAsync(fields.p, host, (size_t)(D + 2) * 2 * sizeof(double),
+                           cudaMemcpyHostToDevice, c->stream));
+  Grid t{2, 1, 1, 2, 2};
+  const double* f = static_cast<const double*>(fields.p);
+  cudaError_t e = c->ops->init(c->model, f, f + 2, f + 2 + 2 * D, c->fix_tmpl.p, t, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "end-state equilibrium launch");
+  LBM_CUDA(cudaStreamSynchronize(c->stream));
+  c->launches += 1;
+  c->fix_axis = axis;
+  c->fix_width = width;
+  c->rec.valid = false;
   return LBM_OK;
 }
 
