@@ -68,6 +68,8 @@ __global__ void __launch_bounds__(128, AdjMinBlocks<S>::value)
   constexpr int Q = Mo::Q, D = Mo::D, RR = Mo::R, NP = Mo::NP;
   const ModelConst& mc = c_mc[M];
   __shared__ double sh[4];
+  wait_prior_grid();     // programmatic launch: the previous step's writes are visible after this
+  allow_next_grid();
 
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y, z = blockIdx.z;

@@ -99,8 +99,23 @@ cudaError_t step_m(const void* src, void* dst, const Grid& g, double omega, int 
   }
   const int bx = cell_block_x(g.nx);
   const dim3 grid((unsigned)((g.nx + bx - 1) / bx), (unsigned)g.ny, (unsigned)g.nz);
+#ifndef LBM_NO_PDL
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(bx);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_stream_collide<M, S>, static_cast<const S*>(src),
+                            static_cast<S*>(dst), g, omega);
+#else
   k_stream_collide<M, S><<<grid, bx, 0, st>>>(static_cast<const S*>(src), static_cast<S*>(dst), g,
                                               omega);
+#endif
   return cudaGetLastError();
 }
 
@@ -131,14 +146,22 @@ cudaError_t adjoint_m(const void* state_n, const void* nu_next, const double* dl
                       double* omega_acc, const Grid& g, double omega, cudaStream_t st) {
   const int bx = cell_block_x(g.nx);
   const dim3 grid((unsigned)((g.nx + bx - 1) / bx), (unsigned)g.ny, (unsigned)g.nz);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(bx);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   if (dldrho)
-    k_adjoint<M, S, L, true><<<grid, bx, 0, st>>>(static_cast<const S*>(state_n), nullptr, dldrho,
-                                                 static_cast<L*>(nu_out), omega_acc, g, omega);
-  else
-    k_adjoint<M, S, L, false><<<grid, bx, 0, st>>>(static_cast<const S*>(state_n),
-                                                  static_cast<const L*>(nu_next), nullptr,
-                                                  static_cast<L*>(nu_out), omega_acc, g, omega);
-  return cudaGetLastError();
+    return cudaLaunchKernelEx(&cfg, k_adjoint<M, S, L, true>, static_cast<const S*>(state_n),
+                              static_cast<const L*>(nullptr), dldrho, static_cast<L*>(nu_out),
+                              omega_acc, g, omega);
+  return cudaLaunchKernelEx(&cfg, k_adjoint<M, S, L, false>, static_cast<const S*>(state_n),
+                            static_cast<const L*>(nu_next), static_cast<const double*>(nullptr),
+                            static_cast<L*>(nu_out), omega_acc, g, omega);
 }
 
 template <int M>

@@ -406,11 +406,24 @@ template <class S>
 struct DirectMinBlocks {
   static constexpr int value = std::is_same<S, double>::value ? 2 : LBM_DIRECT_MINB;
 };
+// Launched with programmatic stream serialization: the next step's grid may be
+// scheduled while this one drains; griddepcontrol.wait holds every thread until
+// the previous grid has completed and its writes are visible (a no-op when the
+// launch has no programmatic dependency).
+__device__ __forceinline__ void wait_prior_grid() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void allow_next_grid() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 template <int M, class S>
 __global__ void __launch_bounds__(128, DirectMinBlocks<S>::value)
     k_stream_collide(const S* __restrict__ src, S* __restrict__ dst, Grid g, double omega) {
   using Mo = Model<M>;
   constexpr int D = Mo::D, RR = Mo::R;
+  wait_prior_grid();
+  allow_next_grid();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= g.nx) return;
   const int y = blockIdx.y, z = blockIdx.z;
