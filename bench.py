@@ -51,7 +51,7 @@ def parse_args(argv=None):
     p.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16", "fp64"])
     p.add_argument("--grid", default="128x64x64", help="NXxNYxNZ of the D3Q95 Riemann workload")
     p.add_argument("--no-extras", action="store_true", help="skip the forms / adjoint / cpu legs")
-    p.add_argument("--leg", default=None, choices=["forms", "adjoint", "large"],
+    p.add_argument("--leg", default=None, choices=["forms", "adjoint", "large", "moments"],
                    help="run one secondary leg alone (for profiling) and print its JSON")
     return p.parse_args(argv)
 
@@ -204,7 +204,8 @@ def run_ours(args):
 
     stream = torch.cuda.current_stream()
     if args.leg:
-        fn = {"forms": forms_leg, "adjoint": adjoint_leg, "large": large_leg}[args.leg]
+        fn = {"forms": forms_leg, "adjoint": adjoint_leg, "large": large_leg,
+              "moments": moments_leg}[args.leg]
         if rank == 0:
             print(json.dumps({"leg": args.leg, "result": fn(lbm, W, stream)}), flush=True)
         return
@@ -271,6 +272,7 @@ def run_ours(args):
         "audit_after": {"nonfinite": audit["nonfinite"], "mass": audit["mass"]},
     }
     if rank == 0 and not args.no_extras:
+        line["moments"] = moments_leg(lbm, W, stream, lat=lat, wl=wl)
         line["e2e"] = e2e_leg(lbm, W, wl, fields, args.steps, stream)
         line["forms"] = forms_leg(lbm, W, stream)
         line["adjoint"] = adjoint_leg(lbm, W, stream)
@@ -311,6 +313,43 @@ def e2e_leg(lbm, W, wl, fields, steps, stream):
     return {"value": round(wl.cells * steps / dt / 1e6, 1), "unit": "MLUPS",
             "h2d_bytes_per_step": round(h2d / steps, 1), "d2h_bytes_per_step": round(d2h / steps, 1),
             "note": "one lbm_init from host fields + %d steps + lbm_moments to host, host clock" % steps}
+
+
+def moments_leg(lbm, W, stream, lat=None, wl=None, calls=200):
+    """lbm_moments into device buffers (rho, U, T in FP64) on the resident state:
+    reads Q populations and writes D + 2 doubles per cell."""
+    import torch
+    own = lat is None
+    if own:
+        wl, fields = W.d3q95_riemann()
+        lat = make_lattice(lbm, wl, fields)
+        lat.step(10)
+    D, Q = lat.info["D"], lat.info["Q"]
+    shape = lat.shape
+    rho = torch.empty(shape, dtype=torch.float64, device="cuda")
+    U = torch.empty((D,) + shape, dtype=torch.float64, device="cuda")
+    T = torch.empty(shape, dtype=torch.float64, device="cuda")
+    for _ in range(5):
+        lbm.lbm_moments(lat.ctx, rho, U, T)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(calls):
+        lbm.lbm_moments(lat.ctx, rho, U, T)
+    b.record(stream)
+    torch.cuda.synchronize()
+    per_call = a.elapsed_time(b) / 1e3 / calls
+    alg = wl.cells * (Q * BYTES[wl.storage] + (D + 2) * 8)
+    peak, _ = hbm_peak()
+    gbs = alg / per_call / 1e9
+    if own:
+        lat.close()
+    return {"workload": wl.name, "storage": wl.storage, "calls": calls,
+            "us_per_call": round(per_call * 1e6, 2),
+            "mcells_per_s": round(wl.cells / per_call / 1e6, 1),
+            "algorithmic_bytes_per_call": alg, "gbs": round(gbs, 1),
+            "frac_of_measured_hbm": round(gbs / peak, 4)}
 
 
 def forms_leg(lbm, W, stream, steps=200):

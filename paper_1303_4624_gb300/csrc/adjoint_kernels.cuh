@@ -40,6 +40,16 @@ struct EqGrad {
   static __device__ __forceinline__ R Dt(R x2) { return (x2 - R(D + 4)) * R(0.25); }
 };
 
+// 4-byte global -> shared copy (cp.async, L1-allocating) and the wait for all of
+// this thread's outstanding copies.
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 __device__ __forceinline__ double block_sum_128(double v, double* sh) {
   v = warp_sum(v);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -52,22 +62,40 @@ __device__ __forceinline__ double block_sum_128(double v, double* sh) {
 }
 
 #ifndef LBM_ADJ_MINB
-#define LBM_ADJ_MINB 4
+#define LBM_ADJ_MINB 3
+#endif
+#ifndef LBM_ADJ_LAM_SMEM
+#define LBM_ADJ_LAM_SMEM 1
 #endif
 template <class S>
 struct AdjMinBlocks {
   static constexpr int value = std::is_same<S, double>::value ? 1 : LBM_ADJ_MINB;
 };
+// FP32 adjoint: the Q gathered lambda_i of a thread live in dynamic shared memory
+// (lambda_i of thread t at word i * 128 + t: conflict-free), which leaves the
+// registers to the gather offsets and the sums (Q floats in registers on top of
+// them spill at 128 registers a thread).  The FP64 adjoint keeps them in registers.
+template <class L>
+struct AdjLamSmem {
+  static constexpr bool value = std::is_same<L, float>::value && LBM_ADJ_LAM_SMEM;
+};
+constexpr int kAdjThreads = 128;
+template <int M, class L>
+constexpr int adj_smem_bytes() {
+  return AdjLamSmem<L>::value ? Model<M>::Q * kAdjThreads * (int)sizeof(L) : 0;
+}
 template <int M, class S, class L, bool kFirst>
-__global__ void __launch_bounds__(128, AdjMinBlocks<S>::value)
+__global__ void __launch_bounds__(kAdjThreads, AdjMinBlocks<S>::value)
     k_adjoint(const S* __restrict__ state, const L* __restrict__ nu_next,
               const double* __restrict__ dldrho, L* __restrict__ nu_out,
               double* __restrict__ omega_acc, Grid g, double omega) {
   using Mo = Model<M>;
   using Rt = L;
   constexpr int Q = Mo::Q, D = Mo::D, RR = Mo::R, NP = Mo::NP;
+  constexpr bool kSm = AdjLamSmem<L>::value;
   const ModelConst& mc = c_mc[M];
   __shared__ double sh[4];
+  extern __shared__ __align__(16) unsigned char adj_dyn[];
   wait_prior_grid();     // programmatic launch: the previous step's writes are visible after this
   allow_next_grid();
 
@@ -84,16 +112,40 @@ __global__ void __launch_bounds__(128, AdjMinBlocks<S>::value)
       if constexpr (D == 3) zo[k] = wrapi(z - (k - RR), g.nz) * g.nxy; else zo[k] = 0;
     });
     const size_t self = ((size_t)z * g.ny + y) * g.nx + x;
-    Rt lam[Q];
     Rt l1 = Rt(0);
     if constexpr (kFirst) l1 = (Rt)dldrho[self];
-    // pass 1: lambda (gathered from x + e_i), forward moments of g (gathered from x - e_i)
+    // lambda_i(x) = nu_next(x + e_i, i): one value per direction for the first step
+    // of the sweep (dL/drho_N, the same for every i), else gathered.
+    Rt lam_r[(kSm || kFirst) ? 1 : Q];
+    const Rt* const lam_s = reinterpret_cast<const Rt*>(adj_dyn) + threadIdx.x;
+    auto lam = [&](int i) -> Rt {
+      if constexpr (kFirst) return l1;
+      else if constexpr (kSm) return lam_s[i * kAdjThreads];
+      else return lam_r[i];
+    };
+    if constexpr (kSm && !kFirst) {
+      // FP32: the lambda gather goes global -> shared by cp.async, which holds no
+      // registers while in flight; each thread waits for its own copies only.
+      Rt* const dst = reinterpret_cast<Rt*>(adj_dyn) + threadIdx.x;
+      cp_async4(dst, nu_next + self);
+      sfor<0, NP>([&](auto P) {
+        constexpr int p = decltype(P)::value;
+        constexpr int ip = 1 + 2 * p, im = 2 + 2 * p;
+        constexpr int ex = Mo::vs.e[ip][0], ey = Mo::vs.e[ip][1], ez = Mo::vs.e[ip][2];
+        const int cm = zo[ez + RR] + yo[ey + RR] + xo[ex + RR];   // x - e_ip
+        const int cp = zo[RR - ez] + yo[RR - ey] + xo[RR - ex];   // x + e_ip
+        cp_async4(dst + ip * kAdjThreads, nu_next + (size_t)ip * g.ncell + cp);
+        cp_async4(dst + im * kAdjThreads, nu_next + (size_t)im * g.ncell + cm);
+      });
+      cp_async_wait_all();
+    }
+    // pass 1: forward moments of g (gathered from x - e_i) and sum lambda_i f_i
     Rt rs, es = Rt(0), jx = Rt(0), jy = Rt(0), jz = Rt(0), sg;
     {
       const Rt h0 = (Rt)Codec<S>::ld(state + self);
-      lam[0] = kFirst ? l1 : nu_next[self];
+      if constexpr (!kSm && !kFirst) lam_r[0] = nu_next[self];
       rs = gW<Rt>(mc, 0) * h0;
-      sg = gW<Rt>(mc, 0) * lam[0] * (Rt(1) + h0);
+      sg = gW<Rt>(mc, 0) * lam(0) * (Rt(1) + h0);
     }
     sfor<0, NP>([&](auto P) {
       constexpr int p = decltype(P)::value;
@@ -104,12 +156,9 @@ __global__ void __launch_bounds__(128, AdjMinBlocks<S>::value)
       const int cp = zo[RR - ez] + yo[RR - ey] + xo[RR - ex];   // x + e_ip
       const Rt hp = (Rt)Codec<S>::ld(state + (size_t)ip * g.ncell + cm);
       const Rt hm = (Rt)Codec<S>::ld(state + (size_t)im * g.ncell + cp);
-      if constexpr (kFirst) {
-        lam[ip] = l1;
-        lam[im] = l1;
-      } else {
-        lam[ip] = nu_next[(size_t)ip * g.ncell + cp];
-        lam[im] = nu_next[(size_t)im * g.ncell + cm];
+      if constexpr (!kSm && !kFirst) {
+        lam_r[ip] = nu_next[(size_t)ip * g.ncell + cp];
+        lam_r[im] = nu_next[(size_t)im * g.ncell + cm];
       }
       const Rt w = gW<Rt>(mc, gg);
       const Rt tr = w * (hp + hm);
@@ -119,7 +168,7 @@ __global__ void __launch_bounds__(128, AdjMinBlocks<S>::value)
       if constexpr (ex != 0) jx += Rt(ex) * tj;
       if constexpr (ey != 0) jy += Rt(ey) * tj;
       if constexpr (ez != 0) jz += Rt(ez) * tj;
-      sg += w * (lam[ip] * (Rt(1) + hp) + lam[im] * (Rt(1) + hm));
+      sg += w * (lam(ip) * (Rt(1) + hp) + lam(im) * (Rt(1) + hm));
     });
     // Linearisation point: the forward moments and temperature of g.  Plain sums in
     // the arithmetic type suffice here (they fix where the Jacobian is taken, to
@@ -141,9 +190,9 @@ __global__ void __launch_bounds__(128, AdjMinBlocks<S>::value)
     const Rt uax = a_r * ux, uay = a_r * uy, uaz = a_r * uz;
 
     // pass 2: contractions with lambda
-    Rt Lr = gW<Rt>(mc, 0) * lam[0] * cf.K0;
-    Rt Sq = gW<Rt>(mc, 0) * lam[0] * gr.Bq(Rt(0));
-    Rt St = gW<Rt>(mc, 0) * lam[0] * gr.Bt(Rt(0));
+    Rt Lr = gW<Rt>(mc, 0) * lam(0) * cf.K0;
+    Rt Sq = gW<Rt>(mc, 0) * lam(0) * gr.Bq(Rt(0));
+    Rt St = gW<Rt>(mc, 0) * lam(0) * gr.Bt(Rt(0));
     Rt Vx = Rt(0), Vy = Rt(0), Vz = Rt(0);
     sfor<0, NP>([&](auto P) {
       constexpr int p = decltype(P)::value;
@@ -166,7 +215,7 @@ __global__ void __launch_bounds__(128, AdjMinBlocks<S>::value)
       const Rt Pqo = s * Rt(-0.5);
       const Rt Pte = gr.Bt(x2) + EqGrad<Rt, D>::Dt(x2) * s2;
       const Rt Pto = EqGrad<Rt, D>::Ct(x2) * s;
-      const Rt ls = lam[ip] + lam[im], ld = lam[ip] - lam[im];
+      const Rt ls = lam(ip) + lam(im), ld = lam(ip) - lam(im);
       Lr += w * (ls * Pe + ld * Po);
       Sq += w * (ls * Pqe + ld * Pqo);
       St += w * (ls * Pte + ld * Pto);
@@ -193,7 +242,7 @@ __global__ void __launch_bounds__(128, AdjMinBlocks<S>::value)
     const Rt om = (Rt)omega;
     const Rt oa = om * alpha, og = om * gam;
     const Rt obx = om * a_r * bx, oby = om * a_r * by, obz = om * a_r * bz;
-    nu_out[self] = om1 * lam[0] + oa;
+    nu_out[self] = om1 * lam(0) + oa;
     sfor<0, NP>([&](auto P) {
       constexpr int p = decltype(P)::value;
       constexpr int ip = 1 + 2 * p, im = 2 + 2 * p;
@@ -204,8 +253,8 @@ __global__ void __launch_bounds__(128, AdjMinBlocks<S>::value)
       if constexpr (ex != 0) od += Rt(ex) * obx;
       if constexpr (ey != 0) od += Rt(ey) * oby;
       if constexpr (ez != 0) od += Rt(ez) * obz;
-      nu_out[(size_t)ip * g.ncell + self] = om1 * lam[ip] + (ev + od);
-      nu_out[(size_t)im * g.ncell + self] = om1 * lam[im] + (ev - od);
+      nu_out[(size_t)ip * g.ncell + self] = om1 * lam(ip) + (ev + od);
+      nu_out[(size_t)im * g.ncell + self] = om1 * lam(im) + (ev - od);
     });
   }
   const double bsum = block_sum_128(om_part, sh);

@@ -21,6 +21,7 @@ struct ModelConst {
   float af;
   double c;
   double T0;           // 1 / (2 c^2), lattice units
+  float T0f, iT0f;     // T0 and 1 / T0 rounded to FP32
   int e[kMaxQc][3];    // lattice vectors in storage order (zero-padded to 3 components)
 };
 

@@ -146,9 +146,29 @@ cudaError_t adjoint_m(const void* state_n, const void* nu_next, const double* dl
                       double* omega_acc, const Grid& g, double omega, cudaStream_t st) {
   const int bx = cell_block_x(g.nx);
   const dim3 grid((unsigned)((g.nx + bx - 1) / bx), (unsigned)g.ny, (unsigned)g.nz);
+  constexpr int smem = adj_smem_bytes<M, L>();
+  if constexpr (smem > 0) {
+    // Dynamic shared memory above the 48 KB default needs the opt-in, once per device.
+    static std::mutex mu;
+    static int done_dev[16] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done_dev[dev & 15] != dev) {
+      e = cudaFuncSetAttribute(k_adjoint<M, S, L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               smem);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_adjoint<M, S, L, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+      done_dev[dev & 15] = dev;
+    }
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = dim3(bx);
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;

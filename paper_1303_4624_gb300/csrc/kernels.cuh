@@ -254,7 +254,44 @@ __device__ __forceinline__ HalfMoments<Rt> half_moments(Get&& hv) {
   return m;
 }
 
-// Cell state from the two halves: FP64 theta recovery, FP32 (or FP64) velocity.
+// Double-float (hi + lo) arithmetic on the FP32 pipe.  On this GPU the FP64 pipe
+// issues about 1/64 of the FP32 rate (two FP64 lanes per SM per clock), so a few
+// dozen FP64 operations per cell already bound a kernel below HBM speed; the
+// temperature recovery and the audit sums use double-float instead.  two_sum is
+// Knuth's error-free addition (s + e = a + b exactly); ff_add adds two
+// double-float numbers and renormalises with Dekker's fast two-sum; the result
+// keeps about 44 significant bits.
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = xadd(a, b);
+  const float bb = xsub(s, a);
+  e = xadd(xsub(a, xsub(s, bb)), xsub(b, bb));
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  e = xadd(e, xadd(a.lo, b.lo));
+  const float h = xadd(s, e);
+  return {h, xsub(e, xsub(h, s))};
+}
+__device__ __forceinline__ FF warp_sum_ff(FF v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    FF w;
+    w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    v = ff_add(v, w);
+  }
+  return v;
+}
+__device__ __forceinline__ double ff_to_double(FF v) { return (double)v.hi + (double)v.lo; }
+
+// Cell state from the two halves: FP32 (or FP64) velocity; theta recovered in FP64
+// (F64 = true: FP32 and FP64 forms) or in FP32 (F64 = false: FP16 / BF16 forms).
+#ifndef LBM_F32_FF
+#define LBM_F32_FF 1
+#endif
 template <class Rt>
 struct CellState {
   Rt q, t, uax, uay, uaz;   // |u|^2, theta - 1, a u
@@ -262,12 +299,90 @@ struct CellState {
   Rt wr, wrd;               // omega rho, omega (rho - 1)
 };
 
-template <int M, class Rt>
+template <int M, class Rt, bool F64 = true>
 __device__ __forceinline__ CellState<Rt> cell_state(const HalfMoments<Rt>& A,
                                                     const HalfMoments<Rt>& B, double omega) {
   constexpr int D = Model<M>::D;
   const ModelConst& mc = c_mc[M];
   CellState<Rt> c;
+  if constexpr (std::is_same<Rt, float>::value && !F64) {
+    // FP16 / BF16 forms: the stored deviations carry a relative rounding of 2^-11
+    // (2^-8 for BF16); the FP32 rounding of the compensated sums (2^-24) is far
+    // below it, so the whole recovery runs on the FP32 pipe.
+    const float rd = xadd(xsub(A.rs, A.rc), xsub(B.rs, B.rc));
+    const float ed = xadd(xsub(A.es, A.ec), xsub(B.es, B.ec));
+    const float jx = xadd(A.jx, B.jx), jy = xadd(A.jy, B.jy), jz = xadd(A.jz, B.jz);
+    const float rho = xadd(1.0f, rd);
+    const float r0 = __fdividef(1.0f, rho);
+    const float ir = xfma(r0, xfma(-rho, r0, 1.0f), r0);   // one Newton step for 1/rho
+    const float a = gA<float>(mc);
+    const float ux = xmul(xmul(a, jx), ir), uy = xmul(xmul(a, jy), ir);
+    const float uz = (D == 3) ? xmul(xmul(a, jz), ir) : 0.0f;
+    c.q = xfma(ux, ux, xfma(uy, uy, xmul(uz, uz)));
+    const float v = xfma(xfma(-(float)D, rd, ed), ir, -c.q);
+    const float y = xmul(v, cst<float>(1.0 / D));
+    c.t = xfma(xfma(-(float)D, y, v), cst<float>(1.0 / D), y);   // unbiased v / D
+    c.uax = xmul(a, ux);
+    c.uay = xmul(a, uy);
+    c.uaz = xmul(a, uz);
+    c.rho = rho;
+    c.rdev = rd;
+    const float om = cst<float>(omega);
+    c.wr = xmul(om, rho);
+    c.wrd = xmul(om, rd);
+    return c;
+  }
+#if LBM_F32_FF
+  if constexpr (std::is_same<Rt, float>::value) {
+    // FP32 form: rho - 1 and E - D rho as double-float on the FP32 pipe
+    FF rd, ed, rho;
+    two_sum(A.rs, B.rs, rd.hi, rd.lo);
+    rd.lo = xsub(rd.lo, xadd(A.rc, B.rc));
+    two_sum(A.es, B.es, ed.hi, ed.lo);
+    ed.lo = xsub(ed.lo, xadd(A.ec, B.ec));
+    two_sum(1.0f, rd.hi, rho.hi, rho.lo);
+    rho.lo = xadd(rho.lo, rd.lo);
+    const float rho_r = xadd(rho.hi, rho.lo);
+    const float r0 = __fdividef(1.0f, rho_r);
+    const float ir = xfma(r0, xsub(xfma(-rho.hi, r0, 1.0f), xmul(rho.lo, r0)), r0);
+    const float ir_lo = xmul(ir, xsub(xfma(-rho.hi, ir, 1.0f), xmul(rho.lo, ir)));
+    const float a = gA<float>(mc);
+    const float jx = xadd(A.jx, B.jx), jy = xadd(A.jy, B.jy), jz = xadd(A.jz, B.jz);
+    const float ux = xmul(xmul(a, jx), ir), uy = xmul(xmul(a, jy), ir);
+    const float uz = (D == 3) ? xmul(xmul(a, jz), ir) : 0.0f;
+    c.q = xfma(ux, ux, xfma(uy, uy, xmul(uz, uz)));
+    // E - D rho = ed - D rd (the product's rounding error recovered by FMA)
+    const float ph = xmul((float)D, rd.hi);
+    const float pl = xfma((float)D, rd.lo, xfma((float)D, rd.hi, -ph));
+    float sh, se;
+    two_sum(ed.hi, -ph, sh, se);
+    const float dl = xadd(se, xsub(ed.lo, pl));
+    const float dh = xadd(sh, dl);
+    const float dlo = xsub(dl, xsub(dh, sh));
+    // (E - D rho) / rho as double-float, then theta - 1 = (that - |u|^2) / D
+    const float xh = xmul(dh, ir);
+    const float xl = xfma(dh, ir_lo, xfma(dlo, ir, xfma(dh, ir, -xh)));
+    // v = x - q as double-float; t = v / D rounded to nearest: a product with the
+    // FP32-rounded 1/D alone is biased (it rounds 1/3 up), which would heat or cool
+    // every cell by a fixed fraction of an ulp per step; one FMA residual step
+    // removes it
+    float vh, ve;
+    two_sum(xh, -c.q, vh, ve);
+    const float vl = xadd(ve, xl);
+    const float third = cst<float>(1.0 / D);
+    const float y = xmul(xadd(vh, vl), third);
+    c.t = xfma(xadd(xfma(-(float)D, y, vh), vl), third, y);
+    c.uax = xmul(a, ux);
+    c.uay = xmul(a, uy);
+    c.uaz = xmul(a, uz);
+    c.rho = rho_r;
+    c.rdev = xadd(rd.hi, rd.lo);
+    const float om = cst<float>(omega);
+    c.wr = xmul(om, rho_r);
+    c.wrd = xmul(om, c.rdev);
+    return c;
+  }
+#endif
   double rd, ed, ir;
   Rt jx, jy, jz, rho_r, ir_r;
   if constexpr (std::is_same<Rt, float>::value) {
@@ -366,6 +481,7 @@ template <class S>
 struct FormOpts {
   static constexpr bool kShell = sizeof(S) == 2;
   static constexpr bool kExact = sizeof(S) >= 4;
+  static constexpr bool kF64Theta = sizeof(S) >= 4;
 };
 
 template <int M, class S, class Load, class Store>
@@ -381,7 +497,7 @@ __device__ __forceinline__ void cell_update(Load&& ld, double omega, Store&& st)
   // a3, a4
   const HalfMoments<Rt> A = half_moments<M, Rt, 0, NH, true, SH>(hv);
   const HalfMoments<Rt> B = half_moments<M, Rt, NH, NP, false, SH>(hv);
-  const CellState<Rt> c = cell_state<M, Rt>(A, B, omega);
+  const CellState<Rt> c = cell_state<M, Rt, FormOpts<S>::kF64Theta>(A, B, omega);
   // a5, a6
   half_collide<M, Rt, 0, NH, true, EX>(c, omega, hv, st);
   half_collide<M, Rt, NH, NP, false, EX>(c, omega, hv, st);
@@ -499,7 +615,7 @@ __device__ __forceinline__ void half_update(Load&& ld, double omega, Store&& st,
   const float* b = &xch[pair][1][0][lane];
   A.rs = a[0]; A.rc = a[32]; A.es = a[64]; A.ec = a[96]; A.jx = a[128]; A.jy = a[160]; A.jz = a[192];
   B.rs = b[0]; B.rc = b[32]; B.es = b[64]; B.ec = b[96]; B.jx = b[128]; B.jy = b[160]; B.jz = b[192];
-  const CellState<Rt> c = cell_state<M, Rt>(A, B, omega);
+  const CellState<Rt> c = cell_state<M, Rt, FormOpts<S>::kF64Theta>(A, B, omega);
   half_collide<M, Rt, P0, P1, HALF == 0, FormOpts<S>::kExact>(c, omega, hv, st);
 }
 
@@ -773,8 +889,122 @@ __device__ __forceinline__ double warp_min(double v) {
   return v;
 }
 
+// ----------------------------------------------------------------- moments, FP32 forms
+// Resident 256-thread blocks per SM the FP32-form moments kernel is register-capped
+// for (64 registers a thread at 4; measured best among 2 to 6).
+#ifndef LBM_MOM_MINB
+#define LBM_MOM_MINB 4
+#endif
+
+// Moments of the FP32 / FP16 / BF16 forms, one thread per cell: the collision's own
+// compensated sums (deviation form, +/- pairs first; rho - 1 and E - D as
+// double-float, j in FP32), then
+//   rho = 1 + rd,  U = j / rho,  T = T0 (1 + ((ed - D rd) / rho - |U|^2 / T0) / D)
+// in FP32 (rho as double-float), written as FP64.  The audit terms of the 256
+// cells of a block are summed in double-float per warp and in FP64 across warps:
+//   mass = n + sum rd,  momentum = sum j,  energy = T0 (D n + sum ed) / 2
+// (rest-state moments: sum w = 1, sum w xi = 0, sum w |xi|^2 = D).
 template <int M, class S>
-__global__ void __launch_bounds__(kMomentThreads)
+__device__ __forceinline__ void moments_fp32_forms(const S* __restrict__ src, const Grid& g,
+                                                   long long idx, double* __restrict__ rho_out,
+                                                   double* __restrict__ U_out,
+                                                   double* __restrict__ T_out,
+                                                   double* __restrict__ partials) {
+  using Mo = Model<M>;
+  constexpr int D = Mo::D, Q = Mo::Q, NH = Mo::NP / 2;
+  constexpr bool SH = sizeof(S) == 2;
+  const ModelConst& mc = c_mc[M];
+  FF srd = {0.f, 0.f}, sed = {0.f, 0.f}, sjx = {0.f, 0.f}, sjy = {0.f, 0.f}, sjz = {0.f, 0.f};
+  float hmin = 3.0e38f, bad = 0.f, cnt = 0.f;
+  if (idx < g.ncell) {
+    auto hv = [&](auto I) {
+      const float v = Codec<S>::ld(src + (size_t)decltype(I)::value * (size_t)g.ncell + idx);
+      hmin = fminf(hmin, v);
+      return v;
+    };
+    const HalfMoments<float> A = half_moments<M, float, 0, NH, true, SH>(hv);
+    const HalfMoments<float> B = half_moments<M, float, NH, Mo::NP, false, SH>(hv);
+    // rs - rc carries the compensated sum of each half; combine the halves exactly
+    two_sum(A.rs, B.rs, srd.hi, srd.lo);
+    srd.lo = xsub(srd.lo, xadd(A.rc, B.rc));
+    two_sum(A.es, B.es, sed.hi, sed.lo);
+    sed.lo = xsub(sed.lo, xadd(A.ec, B.ec));
+    sjx.hi = xadd(A.jx, B.jx);
+    sjy.hi = xadd(A.jy, B.jy);
+    sjz.hi = (D == 3) ? xadd(A.jz, B.jz) : 0.f;
+    FF rho;
+    two_sum(1.0f, srd.hi, rho.hi, rho.lo);
+    rho.lo = xadd(rho.lo, srd.lo);
+    const float r0 = __fdividef(1.0f, rho.hi);
+    const float ir = xfma(r0, xfma(-rho.hi, r0, 1.0f), r0);   // one Newton step for 1/rho
+    const float Ux = xmul(sjx.hi, ir), Uy = xmul(sjy.hi, ir), Uz = xmul(sjz.hi, ir);
+    const float U2 = xfma(Ux, Ux, xfma(Uy, Uy, xmul(Uz, Uz)));
+    const float T0f = mc.T0f;
+    const float dE = xadd(xfma(-(float)D, srd.hi, sed.hi), xfma(-(float)D, srd.lo, sed.lo));
+    const float t = xmul(xsub(xmul(dE, ir), xmul(U2, mc.iT0f)), cst<float>(1.0 / D));
+    if (rho_out) rho_out[idx] = ff_to_double(rho);
+    if (U_out) {
+      U_out[idx] = (double)Ux;
+      U_out[g.ncell + idx] = (double)Uy;
+      if (D == 3) U_out[2 * g.ncell + idx] = (double)Uz;
+    }
+    if (T_out) T_out[idx] = (double)xfma(T0f, t, T0f);
+    if (!isfinite(srd.hi) || !isfinite(sed.hi)) {
+      // a NaN or Inf population poisons both sums: count them one by one
+      for (int i = 0; i < Q; ++i)
+        if (!isfinite((float)Codec<S>::ld(src + (size_t)i * (size_t)g.ncell + idx))) bad = xadd(bad, 1.0f);
+    }
+    cnt = 1.f;
+  }
+  srd = warp_sum_ff(srd);
+  sed = warp_sum_ff(sed);
+  sjx = warp_sum_ff(sjx);
+  sjy = warp_sum_ff(sjy);
+  sjz = warp_sum_ff(sjz);
+  for (int o = 16; o > 0; o >>= 1) {
+    hmin = fminf(hmin, __shfl_xor_sync(0xffffffffu, hmin, o));
+    bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  }
+  // Across the warps of the block: slot k is summed by lane k of warp 0, in
+  // double-float, warp by warp in order (deterministic).
+  constexpr int NW = kMomentThreads / 32;
+  __shared__ FF sh[NW][kAuditSlots];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    sh[wid][0] = srd;
+    sh[wid][1] = sjx;
+    sh[wid][2] = sjy;
+    sh[wid][3] = sjz;
+    sh[wid][4] = sed;
+    sh[wid][5] = {hmin, 0.f};
+    sh[wid][6] = {bad, 0.f};
+    sh[wid][7] = {cnt, 0.f};
+  }
+  __syncthreads();
+  if (threadIdx.x < kAuditSlots) {
+    const int k = threadIdx.x;
+    FF v = sh[0][k];
+    float n = sh[0][7].hi;
+    for (int w = 1; w < NW; ++w) {
+      if (k == 5) v.hi = fminf(v.hi, sh[w][k].hi);
+      else v = ff_add(v, sh[w][k]);
+      n += sh[w][7].hi;                                  // exact: at most 256
+    }
+    double d = ff_to_double(v);
+    if (k == 0) d += (double)n;                                // mass = n + sum (rho - 1)
+    if (k == 4) d = 0.5 * mc.T0 * ((double)D * (double)n + d); // energy
+    if (k == 5) d = (n > 0.f) ? 1.0 + d : 1e300;               // min f / w over the block
+    partials[(size_t)blockIdx.x * kAuditSlots + k] = d;
+  }
+}
+
+template <class S>
+struct MomMinBlocks {
+  static constexpr int value = std::is_same<S, double>::value ? 1 : LBM_MOM_MINB;
+};
+template <int M, class S>
+__global__ void __launch_bounds__(kMomentThreads, MomMinBlocks<S>::value)
     k_moments(const S* __restrict__ src, Grid g, double* __restrict__ rho_out,
               double* __restrict__ U_out, double* __restrict__ T_out,
               double* __restrict__ partials) {
@@ -783,7 +1013,10 @@ __global__ void __launch_bounds__(kMomentThreads)
   const ModelConst& mc = c_mc[M];
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double acc[kAuditSlots] = {0, 0, 0, 0, 0, 1e300, 0, 0};
-  if (idx < g.ncell) {
+  if constexpr (!std::is_same<S, double>::value) {
+    moments_fp32_forms<M, S>(src, g, idx, rho_out, U_out, T_out, partials);
+    return;
+  } else if (idx < g.ncell) {
     double r = 0, mx = 0, my = 0, mz = 0, e2 = 0, mn = 1e300, bad = 0;
     sfor<0, Q>([&](auto I) {
       constexpr int i = decltype(I)::value;

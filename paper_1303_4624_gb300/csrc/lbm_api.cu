@@ -209,6 +209,8 @@ bool build_host_model(int model, HostModel* hm) {
   mc.af = (float)a;
   mc.c = hm->c;
   mc.T0 = 1.0 / (2.0 * hm->c * hm->c);
+  mc.T0f = (float)mc.T0;
+  mc.iT0f = (float)(2.0 * hm->c * hm->c);
   return hm->residual < 1e-13;
 }
 
