@@ -171,16 +171,20 @@ int64_t lbm_steps_done(const lbm_ctx* ctx);
 
 /*
  * lbm_moments - macroscopic fields of the current state (Formula 1, n <= 2):
- *   rho = sum f_i, rho U = sum f_i e_i, D rho T = sum f_i |e_i - U|^2,
- *   computed in FP64 from the stored populations.  Outputs rho [cells],
- *   U [D][cells], T [cells] in `where` memory; any output may be NULL.
+ *   rho = sum f_i, rho U = sum f_i e_i, D rho T = sum f_i |e_i - U|^2.
+ *   FP64 form: summed in FP64.  FP32 / FP16 / BF16 forms: the collision's own
+ *   sums of the deviations (rho - 1 and E - D rho compensated, as double-float),
+ *   fields formed in FP32 (relative error ~1e-7 of the stored state's exact
+ *   fields).  Outputs rho [cells], U [D][cells], T [cells] as FP64 in `where`
+ *   memory; any output may be NULL.
  * Errors: LBM_ESTATE, LBM_EINVAL, LBM_ECUDA.
  */
 int lbm_moments(lbm_ctx* ctx, double* rho, double* U, double* T, int where);
 
 /*
- * lbm_audit - conservation audit of the current state, FP64, deterministic
- * (fixed reduction order).  out[8] (host) receives:
+ * lbm_audit - conservation audit of the current state, deterministic (fixed
+ * reduction order): per-block sums in FP64 (FP64 form) or double-float (other
+ * forms, ~44 significant bits), blocks summed in FP64.  out[8] (host) receives:
  *   [0] mass = sum_x sum_i f_i        [1..3] momentum sum f_i e_i (zero-padded)
  *   [4] energy = sum f_i |e_i|^2 / 2  [5] min over populations of f_i / w_i
  *   [6] number of non-finite populations  [7] number of cells
