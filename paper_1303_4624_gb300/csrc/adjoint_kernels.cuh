@@ -147,11 +147,16 @@ __global__ void __launch_bounds__(kAdjThreads, AdjMinBlocks<S>::value)
       rs = gW<Rt>(mc, 0) * h0;
       sg = gW<Rt>(mc, 0) * lam(0) * (Rt(1) + h0);
     }
+    // Shell by shell: the weight and |xi|^2 are common to a shell, so the pair
+    // terms are summed unweighted and each shell's totals are weighted once.
+    Rt gs = Rt(0), gjx = Rt(0), gjy = Rt(0), gjz = Rt(0), gsg = Rt(0);
     sfor<0, NP>([&](auto P) {
       constexpr int p = decltype(P)::value;
       constexpr int ip = 1 + 2 * p, im = 2 + 2 * p;
       constexpr int gg = Mo::vs.grp[ip];
       constexpr int ex = Mo::vs.e[ip][0], ey = Mo::vs.e[ip][1], ez = Mo::vs.e[ip][2];
+      constexpr bool first = (p == 0) || (Mo::vs.grp[ip - 2] != gg);
+      constexpr bool last = (p + 1 == NP) || (Mo::vs.grp[ip + 2] != gg);
       const int cm = zo[ez + RR] + yo[ey + RR] + xo[ex + RR];   // x - e_ip
       const int cp = zo[RR - ez] + yo[RR - ey] + xo[RR - ex];   // x + e_ip
       const Rt hp = (Rt)Codec<S>::ld(state + (size_t)ip * g.ncell + cm);
@@ -160,15 +165,24 @@ __global__ void __launch_bounds__(kAdjThreads, AdjMinBlocks<S>::value)
         lam_r[ip] = nu_next[(size_t)ip * g.ncell + cp];
         lam_r[im] = nu_next[(size_t)im * g.ncell + cm];
       }
-      const Rt w = gW<Rt>(mc, gg);
-      const Rt tr = w * (hp + hm);
-      rs += tr;
-      es += gX2<Rt>(mc, gg) * tr;
-      const Rt tj = w * (hp - hm);
-      if constexpr (ex != 0) jx += Rt(ex) * tj;
-      if constexpr (ey != 0) jy += Rt(ey) * tj;
-      if constexpr (ez != 0) jz += Rt(ez) * tj;
-      sg += w * (lam(ip) * (Rt(1) + hp) + lam(im) * (Rt(1) + hm));
+      if constexpr (first) gs = gjx = gjy = gjz = gsg = Rt(0);
+      const Rt sp = hp + hm, dm = hp - hm;
+      gs += sp;
+      if constexpr (ex != 0) gjx += Rt(ex) * dm;
+      if constexpr (ey != 0) gjy += Rt(ey) * dm;
+      if constexpr (ez != 0) gjz += Rt(ez) * dm;
+      const Rt lp = lam(ip), lm = lam(im);
+      gsg += lp * hp + lm * hm + (lp + lm);               // lambda_p f_p / w + lambda_m f_m / w
+      if constexpr (last) {
+        const Rt w = gW<Rt>(mc, gg);
+        const Rt tr = w * gs;
+        rs += tr;
+        es += gX2<Rt>(mc, gg) * tr;
+        jx += w * gjx;
+        jy += w * gjy;
+        jz += w * gjz;
+        sg += w * gsg;
+      }
     });
     // Linearisation point: the forward moments and temperature of g.  Plain sums in
     // the arithmetic type suffice here (they fix where the Jacobian is taken, to
@@ -194,35 +208,49 @@ __global__ void __launch_bounds__(kAdjThreads, AdjMinBlocks<S>::value)
     Rt Sq = gW<Rt>(mc, 0) * lam(0) * gr.Bq(Rt(0));
     Rt St = gW<Rt>(mc, 0) * lam(0) * gr.Bt(Rt(0));
     Rt Vx = Rt(0), Vy = Rt(0), Vz = Rt(0);
+    // Per shell, with ls = lambda_p + lambda_m, ld = lambda_p - lambda_m and s = xi_p . u:
+    //   sum ls P = A0 m0 + A2 m2 + m4 / 24 + A1 n1 + n3 / 6,
+    //   sum ls dP/dq = Bq m0 - m2 / 4 - n1 / 2,  sum ls dP/dt = Bt m0 + Dt m2 + Ct n1,
+    // with m0 = sum ls, m2 = sum ls s^2, m4 = sum ls s^4, n1 = sum ld s, n3 = sum ld s^3;
+    // the vector term keeps one v = ld (A1 + s^2/2) + ls s (2 A2 + s^2/6) per pair.
+    Rt m0 = Rt(0), m2 = Rt(0), m4 = Rt(0), n1 = Rt(0), n3 = Rt(0);
+    Rt gvx = Rt(0), gvy = Rt(0), gvz = Rt(0);
     sfor<0, NP>([&](auto P) {
       constexpr int p = decltype(P)::value;
       constexpr int ip = 1 + 2 * p, im = 2 + 2 * p;
       constexpr int gg = Mo::vs.grp[ip];
       constexpr int ex = Mo::vs.e[ip][0], ey = Mo::vs.e[ip][1], ez = Mo::vs.e[ip][2];
+      constexpr bool first = (p == 0) || (Mo::vs.grp[ip - 2] != gg);
+      constexpr bool last = (p + 1 == NP) || (Mo::vs.grp[ip + 2] != gg);
       const Rt x2 = gX2<Rt>(mc, gg);
-      const Rt w = gW<Rt>(mc, gg);
+      const Rt A1 = cf.A1(x2), A2 = cf.A2(x2);
       Rt s = Rt(0);
       if constexpr (ex != 0) s += Rt(ex) * uax;
       if constexpr (ey != 0) s += Rt(ey) * uay;
       if constexpr (ez != 0) s += Rt(ez) * uaz;
       const Rt s2 = s * s;
-      const Rt A1 = cf.A1(x2), A2 = cf.A2(x2);
-      const Rt Pe = cf.A0(x2) + s2 * (A2 + s2 * Rt(1.0 / 24.0));
-      const Rt Po = s * (A1 + s2 * Rt(1.0 / 6.0));
-      const Rt Pse = A1 + s2 * Rt(0.5);
-      const Rt Pso = s * (Rt(2) * A2 + s2 * Rt(1.0 / 6.0));
-      const Rt Pqe = gr.Bq(x2) - s2 * Rt(0.25);
-      const Rt Pqo = s * Rt(-0.5);
-      const Rt Pte = gr.Bt(x2) + EqGrad<Rt, D>::Dt(x2) * s2;
-      const Rt Pto = EqGrad<Rt, D>::Ct(x2) * s;
-      const Rt ls = lam(ip) + lam(im), ld = lam(ip) - lam(im);
-      Lr += w * (ls * Pe + ld * Po);
-      Sq += w * (ls * Pqe + ld * Pqo);
-      St += w * (ls * Pte + ld * Pto);
-      const Rt v = w * (ld * Pse + ls * Pso);
-      if constexpr (ex != 0) Vx += Rt(ex) * v;
-      if constexpr (ey != 0) Vy += Rt(ey) * v;
-      if constexpr (ez != 0) Vz += Rt(ez) * v;
+      const Rt lp = lam(ip), lm = lam(im);
+      const Rt ls = lp + lm, ld = lp - lm;
+      const Rt tl = ls * s2, tu = ld * s;
+      if constexpr (first) m0 = m2 = m4 = n1 = n3 = gvx = gvy = gvz = Rt(0);
+      m0 += ls;
+      m2 += tl;
+      m4 += tl * s2;
+      n1 += tu;
+      n3 += tu * s2;
+      const Rt v = ld * (A1 + s2 * Rt(0.5)) + (ls * s) * (Rt(2) * A2 + s2 * Rt(1.0 / 6.0));
+      if constexpr (ex != 0) gvx += Rt(ex) * v;
+      if constexpr (ey != 0) gvy += Rt(ey) * v;
+      if constexpr (ez != 0) gvz += Rt(ez) * v;
+      if constexpr (last) {
+        const Rt w = gW<Rt>(mc, gg);
+        Lr += w * (cf.A0(x2) * m0 + A2 * m2 + m4 * Rt(1.0 / 24.0) + A1 * n1 + n3 * Rt(1.0 / 6.0));
+        Sq += w * (gr.Bq(x2) * m0 - m2 * Rt(0.25) - n1 * Rt(0.5));
+        St += w * (gr.Bt(x2) * m0 + EqGrad<Rt, D>::Dt(x2) * m2 + EqGrad<Rt, D>::Ct(x2) * n1);
+        Vx += w * gvx;
+        Vy += w * gvy;
+        Vz += w * gvz;
+      }
     });
     // chain rule to the moments (arithmetic type; the omega term in FP64)
     const Rt Lux = rho_r * (a_r * Vx + Rt(2) * ux * Sq);
