@@ -283,6 +283,44 @@ int64_t lbm_launch_count(const lbm_ctx* ctx);
 int lbm_audit_noalloc(int model, int storage, const int64_t dims[3], const void* h, double* out,
                       void* stream);
 
+/*
+ * lbm_equation_count - Omega(m, D), the number of moment equations of Formula 5
+ * up to n_max = 2m for the m-th order Hermite equilibrium (Formulas 6-8, Table 1),
+ * from the generating function of partitions into at most D parts (Formula 7).
+ *   m in [0, 7], D in [1, 4]; *out receives the count.  Host only.
+ * Errors: LBM_EINVAL.
+ */
+int lbm_equation_count(int m, int D, int64_t* out);
+
+/*
+ * lbm_generate_model - an on-lattice isotropic velocity set of order m in D
+ * dimensions (Formulas 4, 5, 9, 10): each representative expands into its orbit
+ * under coordinate permutations and sign changes (the groups G_k before
+ * Formula 9, one weight per orbit), and the group weights and the scale c solve
+ * Formula 5 up to n_max = 2m.  Host only; needs no GPU.
+ *   D in [1, 4], m in [0, 7];
+ *   reps:    [ngroups][D] integers in [-8, 8] (signs and order do not matter),
+ *            ngroups = Omega(m, D) - 1 (Formula 10), distinct orbits;
+ *   which:   index among the solutions with all weights positive, by increasing c;
+ *   qmax:    capacity of e / w in velocities;
+ *   Q:       (out) the number of velocities, set even when qmax is too small;
+ *   e, w:    (out, may be NULL) velocities [Q][D] (integer lattice vectors, orbit
+ *            by orbit in the order of reps, each orbit in decreasing lexicographic
+ *            order) and their weights [Q] (sum w = 1);
+ *   c:       (out) the lattice scale, v_i = c e_i;
+ *   residual:(out, may be NULL) max |Formula 5 residual| (normalised moments);
+ *   nsolutions: (out, may be NULL) number of solutions with positive weights.
+ * Method: for fixed 1/c^2 the equations are linear in the weights with one
+ * equation more than unknowns; the positive roots of the determinant of the
+ * augmented system (a polynomial of degree <= m in 1/c^2) are bracketed and
+ * bisected, the weights follow by least squares, and Newton's method on the full
+ * system polishes (W, c).  Errors: LBM_EINVAL (Formula 10 not met, repeated orbit,
+ * entry out of range, qmax too small, no solution with positive weights, which
+ * out of range).
+ */
+int lbm_generate_model(int D, int m, int ngroups, const int* reps, int which, int qmax, int* Q,
+                       int* e, double* w, double* c, double* residual, int* nsolutions);
+
 /* lbm_strerror - static text for an error code; lbm_last_error - detail of
  * the last failure on the calling thread (empty string if none). */
 const char* lbm_strerror(int code);

@@ -20,7 +20,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblbm_gb300.so")
 
 UNITS = ["k_fp64.cu", "k_fp32.cu", "k_fp16.cu", "k_bf16.cu", "lbm_api.cu", "adjoint.cu",
-         "audit_noalloc.cu"]
+         "audit_noalloc.cu", "model_gen.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-ffp-contract=off", "-I", INC]

@@ -45,7 +45,8 @@ SYMBOLS = ("lbm_model_info", "lbm_set_allocator", "lbm_create", "lbm_destroy", "
            "lbm_init", "lbm_step", "lbm_steps_done", "lbm_moments", "lbm_audit",
            "lbm_get_populations", "lbm_set_populations", "lbm_get_raw", "lbm_set_raw",
            "lbm_record", "lbm_record_bounded", "lbm_backward", "lbm_release_record", "lbm_synchronize",
-           "lbm_launch_count", "lbm_audit_noalloc", "lbm_strerror", "lbm_last_error")
+           "lbm_launch_count", "lbm_audit_noalloc", "lbm_equation_count", "lbm_generate_model",
+           "lbm_strerror", "lbm_last_error")
 
 _vp, _i, _i64, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -76,6 +77,9 @@ _sig = {
     "lbm_synchronize": (_i, [_vp]),
     "lbm_launch_count": (_i64, [_vp]),
     "lbm_audit_noalloc": (_i, [_i, _i, ctypes.POINTER(_i64), _vp, _vp, _vp]),
+    "lbm_equation_count": (_i, [_i, _i, ctypes.POINTER(_i64)]),
+    "lbm_generate_model": (_i, [_i, _i, _i, _vp, _i, _i, ctypes.POINTER(_i), _vp, _vp,
+                                ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_i)]),
     "lbm_strerror": (ctypes.c_char_p, [_i]),
     "lbm_last_error": (ctypes.c_char_p, []),
 }
@@ -160,6 +164,34 @@ def lbm_model_info(model):
                                ctypes.byref(T0)), "lbm_model_info")
     return {"Q": Q.value, "D": D.value, "reach": R.value, "e": e, "w": w, "c": c.value,
             "T0": T0.value}
+
+
+def lbm_equation_count(m, D):
+    """Omega(m, D): the number of moment equations of Formula 5 up to n_max = 2m (Table 1)."""
+    out = _i64()
+    _check(_lib.lbm_equation_count(int(m), int(D), ctypes.byref(out)), "lbm_equation_count")
+    return out.value
+
+
+def lbm_generate_model(D, m, reps, which=0):
+    """Velocity set of order m in D dimensions from one representative per symmetry
+    group (Formulas 5, 9, 10): dict(Q, e [Q, D] int32, w [Q], c, residual, nsolutions).
+    Runs on the host; needs no GPU."""
+    reps = np.ascontiguousarray(np.asarray(reps, dtype=np.int32).reshape(-1, int(D)))
+    Q, c, res, nsol = _i(), _d(), _d(), _i()
+    rc = _lib.lbm_generate_model(int(D), int(m), reps.shape[0], reps.ctypes.data, int(which), 0,
+                                 ctypes.byref(Q), None, None, ctypes.byref(c), ctypes.byref(res),
+                                 ctypes.byref(nsol))
+    if rc != LBM_OK and Q.value == 0:
+        raise LbmError(rc, "lbm_generate_model")
+    e = np.zeros((Q.value, int(D)), dtype=np.int32)
+    w = np.zeros(Q.value)
+    _check(_lib.lbm_generate_model(int(D), int(m), reps.shape[0], reps.ctypes.data, int(which),
+                                   Q.value, ctypes.byref(Q), e.ctypes.data, w.ctypes.data,
+                                   ctypes.byref(c), ctypes.byref(res), ctypes.byref(nsol)),
+           "lbm_generate_model")
+    return {"Q": Q.value, "e": e, "w": w, "c": c.value, "residual": res.value,
+            "nsolutions": nsol.value}
 
 
 def lbm_create(model, dims, omega, storage, stream=None, torch_allocator=True):

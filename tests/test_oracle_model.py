@@ -118,3 +118,18 @@ def test_reference_temperature():
         e = mdl.e.astype(float)
         assert math.isclose(float(np.sum(mdl.w * e[:, 0] ** 2)), mdl.T0, rel_tol=1e-13)
         assert math.isclose(float(np.sum(mdl.w * xi[:, 0] ** 2)), 1.0, rel_tol=1e-13)
+
+
+@pytest.mark.parametrize("reps,W,start", [
+    (((0, 0), (1, 0), (1, 1)), (4 / 9, 1 / 9, 1 / 36), (0.5, 0.1, 0.03)),
+    (((0, 0, 0), (1, 0, 0), (1, 1, 1)), (2 / 9, 1 / 9, 1 / 72), (0.25, 0.1, 0.02)),
+    (((0, 0, 0), (1, 0, 0), (1, 1, 0)), (1 / 3, 1 / 18, 1 / 36), (0.3, 0.05, 0.03)),
+])
+def test_general_solver_reproduces_textbook_second_order_sets(reps, W, start):
+    """Formula 10 admits three groups at m = 2 (Omega(2, D) = 4): the Newton solve of
+    Formula 5 from a start away from the solution lands on the textbook D2Q9, D3Q15
+    and D3Q19 weights with c^2 = 3/2."""
+    assert M.omega_count(2, len(reps[0])) == len(reps) + 1
+    Ws, c = M.solve_weights(reps, start, 1.1, m=2)
+    assert math.isclose(c * c, 1.5, rel_tol=1e-14)
+    assert np.allclose(Ws, W, rtol=1e-13, atol=0)
