@@ -287,11 +287,9 @@ __device__ __forceinline__ FF warp_sum_ff(FF v) {
 }
 __device__ __forceinline__ double ff_to_double(FF v) { return (double)v.hi + (double)v.lo; }
 
-// Cell state from the two halves: FP32 (or FP64) velocity; theta recovered in FP64
-// (F64 = true: FP32 and FP64 forms) or in FP32 (F64 = false: FP16 / BF16 forms).
-#ifndef LBM_F32_FF
-#define LBM_F32_FF 1
-#endif
+// Cell state from the two halves.  theta - 1 is recovered in double-float on the
+// FP32 pipe for the FP32 form (F64 = true, Rt = float), in FP32 for the FP16 / BF16
+// forms (F64 = false) and in FP64 for the FP64 form (Rt = double).
 template <class Rt>
 struct CellState {
   Rt q, t, uax, uay, uaz;   // |u|^2, theta - 1, a u
@@ -332,7 +330,6 @@ __device__ __forceinline__ CellState<Rt> cell_state(const HalfMoments<Rt>& A,
     c.wrd = xmul(om, rd);
     return c;
   }
-#if LBM_F32_FF
   if constexpr (std::is_same<Rt, float>::value) {
     // FP32 form: rho - 1 and E - D rho as double-float on the FP32 pipe
     FF rd, ed, rho;
@@ -381,45 +378,28 @@ __device__ __forceinline__ CellState<Rt> cell_state(const HalfMoments<Rt>& A,
     c.wr = xmul(om, rho_r);
     c.wrd = xmul(om, c.rdev);
     return c;
-  }
-#endif
-  double rd, ed, ir;
-  Rt jx, jy, jz, rho_r, ir_r;
-  if constexpr (std::is_same<Rt, float>::value) {
-    rd = xadd(xsub((double)A.rs, (double)A.rc), xsub((double)B.rs, (double)B.rc));
-    ed = xadd(xsub((double)A.es, (double)A.ec), xsub((double)B.es, (double)B.ec));
-    jx = xadd(A.jx, B.jx);
-    jy = xadd(A.jy, B.jy);
-    jz = xadd(A.jz, B.jz);
-    const double rho_d = xadd(1.0, rd);
-    rho_r = (float)rho_d;
-    ir = (double)__fdividef(1.0f, rho_r);
-    ir = xfma(ir, xfma(-rho_d, ir, 1.0), ir);     // Newton's method for 1/rho
-    ir_r = (float)ir;                             // 1/rho rounded to FP32
   } else {
-    rd = xadd(A.rs, B.rs);
-    ed = xadd(A.es, B.es);
-    jx = xadd(A.jx, B.jx);
-    jy = xadd(A.jy, B.jy);
-    jz = xadd(A.jz, B.jz);
-    rho_r = xadd(1.0, rd);
-    ir_r = 1.0 / rho_r;
-    ir = ir_r;
+    // FP64 form: everything in FP64
+    const double rd = xadd(A.rs, B.rs);
+    const double ed = xadd(A.es, B.es);
+    const double jx = xadd(A.jx, B.jx), jy = xadd(A.jy, B.jy), jz = xadd(A.jz, B.jz);
+    const double rho = xadd(1.0, rd);
+    const double ir = 1.0 / rho;
+    const double a = gA<double>(mc);
+    const double ux = xmul(xmul(a, jx), ir), uy = xmul(xmul(a, jy), ir);
+    const double uz = (D == 3) ? xmul(xmul(a, jz), ir) : 0.0;
+    c.q = xfma(ux, ux, xfma(uy, uy, xmul(uz, uz)));
+    // theta - 1 = ((E - D rho) / rho - |u|^2) / D
+    c.t = xmul(xfma(xfma(-(double)D, rd, ed), ir, -c.q), 1.0 / D);
+    c.uax = xmul(a, ux);
+    c.uay = xmul(a, uy);
+    c.uaz = xmul(a, uz);
+    c.rho = rho;
+    c.rdev = rd;
+    c.wr = xmul(omega, rho);
+    c.wrd = xmul(omega, rd);
+    return c;
   }
-  const Rt a = gA<Rt>(mc);
-  const Rt ux = xmul(xmul(a, jx), ir_r), uy = xmul(xmul(a, jy), ir_r);
-  const Rt uz = (D == 3) ? xmul(xmul(a, jz), ir_r) : Rt(0);
-  c.q = xfma(ux, ux, xfma(uy, uy, xmul(uz, uz)));
-  // theta - 1 = ((E - D rho) / rho - |u|^2) / D, in FP64
-  c.t = (Rt)xmul(xfma(xfma(-(double)D, rd, ed), ir, -(double)c.q), 1.0 / D);
-  c.uax = xmul(a, ux);
-  c.uay = xmul(a, uy);
-  c.uaz = xmul(a, uz);
-  c.rho = rho_r;
-  c.rdev = (Rt)rd;
-  c.wr = xmul((Rt)omega, rho_r);
-  c.wrd = (Rt)xmul(omega, rd);
-  return c;
 }
 
 // Equilibrium + BGK of pairs [P0, P1) (and the rest direction when REST), with
