@@ -421,6 +421,7 @@ __device__ __forceinline__ void half_collide(const CellState<Rt>& c, double omeg
   const EqCoef<Rt, D> cf(c.q, c.t);
   const Rt om = cst<Rt>(omega);
   const Rt om1 = cst<Rt>(1.0 - omega);
+  const Rt wr24 = xmul(c.wr, cst<Rt>(1.0 / 24.0)), wr6 = xmul(c.wr, cst<Rt>(1.0 / 6.0));
   if constexpr (REST) {
     const Rt h0 = hv(std::integral_constant<int, 0>{});
     if constexpr (EXACT)
@@ -436,18 +437,20 @@ __device__ __forceinline__ void half_collide(const CellState<Rt>& c, double omeg
     const Rt x2 = gX2<Rt>(mc, gg);
     const Rt s = edot<Rt, ex, ey, ez>(c.uax, c.uay, c.uaz);
     const Rt s2 = xmul(s, s);
-    const Rt ev = xfma(s2, xfma(s2, cst<Rt>(1.0 / 24.0), cf.A2(x2)), cf.A0m1(x2));
-    const Rt od = xmul(s, xfma(s2, cst<Rt>(1.0 / 6.0), cf.A1(x2)));
     const Rt hp = hv(std::integral_constant<int, ip>{});
     const Rt hm = hv(std::integral_constant<int, im>{});
     if constexpr (EXACT) {
+      const Rt ev = xfma(s2, xfma(s2, cst<Rt>(1.0 / 24.0), cf.A2(x2)), cf.A0m1(x2));
+      const Rt od = xmul(s, xfma(s2, cst<Rt>(1.0 / 6.0), cf.A1(x2)));
       const Rt be = xfma(c.rho, ev, c.rdev);      // even part of h^eq
       const Rt bo = xmul(c.rho, od);              // odd part of h^eq
       st(std::integral_constant<int, ip>{}, xfma(om, xsub(xadd(be, bo), hp), hp));
       st(std::integral_constant<int, im>{}, xfma(om, xsub(xsub(be, bo), hm), hm));
     } else {
-      const Rt base = xfma(c.wr, ev, c.wrd);
-      const Rt wod = xmul(c.wr, od);
+      // omega rho folded into the shell's coefficients: base = omega h^eq's even
+      // part, wod = its odd part
+      const Rt base = xfma(s2, xfma(s2, wr24, xmul(c.wr, cf.A2(x2))), xfma(c.wr, cf.A0m1(x2), c.wrd));
+      const Rt wod = xmul(s, xfma(s2, wr6, xmul(c.wr, cf.A1(x2))));
       st(std::integral_constant<int, ip>{}, xfma(om1, hp, xadd(base, wod)));
       st(std::integral_constant<int, im>{}, xfma(om1, hm, xsub(base, wod)));
     }
