@@ -179,8 +179,12 @@ def time_steps(lbm, lat, steps, warmup, stream):
     return start.elapsed_time(stop) / 1e3
 
 
+GRAPH_STEPS = 32     # steps per CUDA-graph replay in lbm_step (captured before timing)
+
+
 def make_lattice(lbm, wl, fields, storage=None):
     lat = lbm.Lattice(wl.model, wl.dims, wl.omega, storage or wl.storage)
+    lbm.lbm_set_graph_steps(lat.ctx, GRAPH_STEPS)
     lat.init(fields.rho, fields.U, fields.theta * lat.info["T0"])
     return lat
 
@@ -258,9 +262,13 @@ def run_ours(args):
         "config": {"workload": wl.name, "model": "D3Q95",
                    "storage": "%s (deviation h = f/w - 1)" % wl.storage,
                    "grid": "%dx%dx%d" % wl.dims, "omega": wl.omega, "cells": wl.cells,
-                   "l2": "inputs larger than L2 (2 x %.0f MB state vs 129 MB L2)"
+                   "l2": ("inputs larger than L2 (2 x %.0f MB state vs 129 MB L2)"
+                          if 2 * wl.cells * Q * BYTES[wl.storage] > 129e6 else
+                          "L2-resident (2 x %.0f MB state vs 129 MB L2): no roofline claim")
                          % (wl.cells * Q * BYTES[wl.storage] / 1e6),
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "launch": "CUDA graphs of %d steps (programmatic dependent launch between "
+                             "steps), remainder launched directly" % GRAPH_STEPS},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"
                      if peak_kind == "measured" else "fallback 6.8 TB/s",
@@ -295,6 +303,7 @@ def e2e_leg(lbm, W, wl, fields, steps, stream):
     rho = torch.from_numpy(fields.rho).pin_memory().numpy()
     U = torch.from_numpy(np.ascontiguousarray(fields.U)).pin_memory().numpy()
     lat = lbm.Lattice(wl.model, wl.dims, wl.omega, wl.storage)
+    lbm.lbm_set_graph_steps(lat.ctx, GRAPH_STEPS)
     T = torch.from_numpy(fields.theta * lat.info["T0"]).pin_memory().numpy()
     out_r = torch.empty(fields.rho.shape, dtype=torch.float64).pin_memory().numpy()
     out_U = torch.empty((D,) + fields.rho.shape, dtype=torch.float64).pin_memory().numpy()

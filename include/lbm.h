@@ -133,6 +133,21 @@ int lbm_set_omega(lbm_ctx* ctx, double omega);
 int lbm_set_variant(lbm_ctx* ctx, int variant);
 
 /*
+ * lbm_set_graph_steps - lbm_step replays runs of `steps` launches from a CUDA
+ * graph (captured on a stream the library owns, by this call for both starting
+ * buffers and again on the first lbm_step after a change that invalidates them,
+ * and launched on the context's stream) whenever
+ * the default direct kernel is in use and at least 2 * steps steps are asked for;
+ * the remainder is launched directly.  Results are bitwise those of direct
+ * launches.  steps: 0 (launch every step directly) or an even number <= 4096;
+ * default 32.  A graph is recaptured after lbm_set_omega, lbm_set_variant or
+ * lbm_set_fixed_ends.  Do not call lbm_step while another thread captures the
+ * context's stream.  If a capture fails the context falls back to direct launches
+ * (this call then returns LBM_ECUDA).  Errors: LBM_EINVAL, LBM_ECUDA.
+ */
+int lbm_set_graph_steps(lbm_ctx* ctx, int steps);
+
+/*
  * lbm_set_fixed_ends - the end conditions of the paper's shock tube (paragraph
  * before Figure 1: the left and right boundary planes carry the fixed states C_L
  * and C_R).  After every later lbm_step the first and the last `width` planes

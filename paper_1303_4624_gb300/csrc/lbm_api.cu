@@ -310,7 +310,27 @@ int DevBuf::ensure(size_t nbytes, cudaStream_t st) {
 }  // namespace lbm
 
 // ================================================================ context
+// Steps replayed from a CUDA graph: kGraphSteps launches (an even count, so a replay
+// leaves the ping-pong buffers where it found them) captured once per context on a
+// library-owned stream and launched on the caller's stream.  One graph per starting
+// buffer; recaptured when omega, the kernel variant or the end planes change.
+constexpr int kGraphSteps = 32;
+struct StepGraph {
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  void reset() {
+    for (auto& e : exec)
+      if (e) {
+        cudaGraphExecDestroy(e);
+        e = nullptr;
+      }
+  }
+};
+
 struct lbm_ctx {
+  ~lbm_ctx() {
+    graph.reset();
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+  }
   int model = 0, storage = 0, dev = 0, D = 0, Q = 0;
   const StorageOps* ops = nullptr;
   Grid g{};
@@ -330,6 +350,9 @@ struct lbm_ctx {
   int64_t steps = 0;
   int64_t launches = 0;
   Record rec;         // checkpointed rollout (adjoint.h)
+  int graph_steps = kGraphSteps;   // 0: launch every step directly
+  StepGraph graph;
+  cudaStream_t cap_stream = nullptr;
 };
 
 namespace {
@@ -350,21 +373,65 @@ int pick_variant(const lbm_ctx* c) {
   return kVariantDirect;
 }
 
-int do_steps(lbm_ctx* c, int64_t n) {
-  const int variant = pick_variant(c);
+// n steps enqueued on stream st starting from buffer *cur (which is advanced).
+cudaError_t enqueue_steps(lbm_ctx* c, int64_t n, int variant, int* cur, cudaStream_t st) {
   for (int64_t k = 0; k < n; ++k) {
-    cudaError_t e = c->ops->step(c->model, c->state[c->cur].p, c->state[c->cur ^ 1].p, c->g,
-                                 c->omega, variant, static_cast<int*>(c->status.p), c->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "stream_collide launch");
-    c->cur ^= 1;
-    c->launches += 1;
+    cudaError_t e = c->ops->step(c->model, c->state[*cur].p, c->state[*cur ^ 1].p, c->g, c->omega,
+                                 variant, static_cast<int*>(c->status.p), st);
+    if (e != cudaSuccess) return e;
+    *cur ^= 1;
     if (c->fix_width > 0) {
-      e = c->ops->fix_ends(c->state[c->cur].p, c->g, c->fix_axis, c->fix_width, c->fix_tmpl.p, c->Q,
-                           c->stream);
-      if (e != cudaSuccess) return cuda_fail(e, "fix_ends launch");
-      c->launches += 1;
+      e = c->ops->fix_ends(c->state[*cur].p, c->g, c->fix_axis, c->fix_width, c->fix_tmpl.p, c->Q,
+                           st);
+      if (e != cudaSuccess) return e;
     }
   }
+  return cudaSuccess;
+}
+
+// Capture kGraphSteps steps starting from buffer `parity`.  False (and graphs off for
+// this context) if capture or instantiation fails; the caller then launches directly.
+bool capture_steps(lbm_ctx* c, int parity, int variant) {
+  if (!c->cap_stream &&
+      cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    c->graph_steps = 0;
+    return false;
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    int cur = parity;
+    const cudaError_t le = enqueue_steps(c, c->graph_steps, variant, &cur, c->cap_stream);
+    e = cudaStreamEndCapture(c->cap_stream, &graph);
+    if (le != cudaSuccess) e = le;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph.exec[parity], graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    c->graph.exec[parity] = nullptr;
+    c->graph_steps = 0;
+    return false;
+  }
+  return true;
+}
+
+int do_steps(lbm_ctx* c, int64_t n) {
+  const int variant = pick_variant(c);
+  const int64_t per_step = c->fix_width > 0 ? 2 : 1;
+  int64_t done = 0;
+  if (c->graph_steps > 0 && variant == kVariantDirect && n >= 2 * c->graph_steps &&
+      (c->graph.exec[c->cur] || capture_steps(c, c->cur, variant))) {
+    for (; n - done >= c->graph_steps; done += c->graph_steps) {
+      cudaError_t e = cudaGraphLaunch(c->graph.exec[c->cur], c->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "step graph launch");
+      c->launches += per_step * c->graph_steps;
+    }
+  }
+  cudaError_t e = enqueue_steps(c, n - done, variant, &c->cur, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "stream_collide launch");
+  c->launches += per_step * (n - done);
   c->steps += n;
   return LBM_OK;
 }
@@ -521,6 +588,23 @@ int lbm_set_omega(lbm_ctx* c, double omega) {
   if (!(omega >= 0.0 && omega < 2.0)) return fail(LBM_EINVAL, "omega = %g outside [0, 2)", omega);
   c->omega = omega;
   c->rec.valid = false;
+  c->graph.reset();
+  return LBM_OK;
+}
+
+int lbm_set_graph_steps(lbm_ctx* c, int steps) {
+  if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+  if (steps < 0 || steps % 2 || steps > 4096)
+    return fail(LBM_EINVAL, "graph steps must be 0 or an even number <= 4096 (got %d)", steps);
+  DeviceGuard dg(c->dev);
+  c->graph.reset();
+  c->graph_steps = steps;
+  // capture both starting buffers now, so that no later lbm_step pays for it
+  const int variant = pick_variant(c);
+  if (steps > 0 && variant == kVariantDirect)
+    for (int parity = 0; parity < 2; ++parity)
+      if (!capture_steps(c, parity, variant))
+        return fail(LBM_ECUDA, "graph capture of the step failed; direct launches stay in use");
   return LBM_OK;
 }
 
@@ -534,6 +618,7 @@ int lbm_set_variant(lbm_ctx* c, int variant) {
   if (variant == kVariantStaged && !staged_applicable(c->g))
     return fail(LBM_EINVAL, "the staged kernel needs Nx %% 8 == 0");
   c->variant = variant;
+  c->graph.reset();
   return LBM_OK;
 }
 
@@ -541,6 +626,7 @@ int lbm_set_fixed_ends(lbm_ctx* c, int axis, int width, const double* lo, const 
   if (!c) return fail(LBM_EINVAL, "ctx is NULL");
   if (width == 0) {
     c->fix_width = 0;
+    c->graph.reset();
     return LBM_OK;
   }
   if (axis < 0 || axis >= c->D) return fail(LBM_EINVAL, "axis %d", axis);
@@ -577,6 +663,7 @@ int lbm_set_fixed_ends(lbm_ctx* c, int axis, int width, const double* lo, const 
   c->fix_axis = axis;
   c->fix_width = width;
   c->rec.valid = false;
+  c->graph.reset();
   return LBM_OK;
 }
 

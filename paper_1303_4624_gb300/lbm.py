@@ -41,7 +41,7 @@ ADJ_DTYPE = {LBM_FP64: np.float64, LBM_FP32: np.float32, LBM_FP16DEV: np.float32
 
 # exported symbols of include/lbm.h
 SYMBOLS = ("lbm_model_info", "lbm_set_allocator", "lbm_create", "lbm_destroy", "lbm_set_omega",
-           "lbm_set_variant", "lbm_set_fixed_ends", "lbm_set_stream",
+           "lbm_set_variant", "lbm_set_graph_steps", "lbm_set_fixed_ends", "lbm_set_stream",
            "lbm_init", "lbm_step", "lbm_steps_done", "lbm_moments", "lbm_audit",
            "lbm_get_populations", "lbm_set_populations", "lbm_get_raw", "lbm_set_raw",
            "lbm_record", "lbm_record_bounded", "lbm_backward", "lbm_release_record", "lbm_synchronize",
@@ -59,6 +59,7 @@ _sig = {
     "lbm_destroy": (_i, [_vp]),
     "lbm_set_omega": (_i, [_vp, _d]),
     "lbm_set_variant": (_i, [_vp, _i]),
+    "lbm_set_graph_steps": (_i, [_vp, _i]),
     "lbm_set_fixed_ends": (_i, [_vp, _i, _i, _vp, _vp]),
     "lbm_set_stream": (_i, [_vp, _vp]),
     "lbm_init": (_i, [_vp, _vp, _vp, _vp, _i]),
@@ -221,6 +222,11 @@ def lbm_set_omega(ctx, omega):
 
 def lbm_set_variant(ctx, variant):
     _check(_lib.lbm_set_variant(ctx, int(variant)), "lbm_set_variant")
+
+
+def lbm_set_graph_steps(ctx, steps):
+    """Steps per CUDA-graph replay in lbm_step (0: direct launches; default 32)."""
+    _check(_lib.lbm_set_graph_steps(ctx, int(steps)), "lbm_set_graph_steps")
 
 
 def lbm_set_fixed_ends(ctx, axis, width, lo=None, hi=None):
