@@ -67,6 +67,23 @@ def test_d2q33_fp64_riemann_256x8_200_steps(lbm):
     compare(mdl, S, lat, TOL["fp64"])
 
 
+@pytest.mark.parametrize("storage,tol", [("fp32", TOL["fp32"]), ("fp16", 1e-3), ("bf16", 1e-2)])
+def test_d2q33_reduced_precision_forms(lbm, storage, tol):
+    """The D2Q33 workload's states on 256 x 8, 100 steps, in the FP32 form (1e-5)
+    and the FP16 / BF16 deviation forms (1e-3 / 1e-2, their storage rounding).
+    D2Q33's weights span five decades (3.5e-6 to 0.16); the deviation storage
+    h = f/w - 1 keeps every direction in the same range."""
+    fields = W.riemann_planar(2, 256, 8, 1, 128, (1.0, 1.0), (0.5, 0.8), seed=2)
+    mdl, S, lat = run_both(lbm, "D2Q33", storage, fields, 1.5, 100, (256, 8, 1))
+    rho, U, T = lat.moments()
+    r0, U0, T0 = olbm.macroscopic(mdl, S)
+    err = max(np.max(np.abs(rho - r0) / r0), np.max(np.abs(T - T0) / T0),
+              np.max(np.abs(U - U0)) / np.sqrt(mdl.T0))
+    assert err <= tol, err
+    a = lat.audit()
+    assert a["nonfinite"] == 0
+
+
 @pytest.mark.parametrize("variant", [1, 3])
 @pytest.mark.parametrize("storage", ["fp64", "fp32"])
 def test_d3q95_riemann_ragged_grid(lbm, storage, variant):
