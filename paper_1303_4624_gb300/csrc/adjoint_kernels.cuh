@@ -105,12 +105,7 @@ __global__ void __launch_bounds__(kAdjThreads, AdjMinBlocks<S>::value)
   double om_part = 0.0;
   if (active) {
     int xo[2 * RR + 1], yo[2 * RR + 1], zo[2 * RR + 1];
-    sfor<0, 2 * RR + 1>([&](auto K) {
-      constexpr int k = decltype(K)::value;
-      xo[k] = wrapi(x - (k - RR), g.nx);
-      yo[k] = wrapi(y - (k - RR), g.ny) * g.nx;
-      if constexpr (D == 3) zo[k] = wrapi(z - (k - RR), g.nz) * g.nxy; else zo[k] = 0;
-    });
+    neighbour_offsets<D, RR>(x, y, z, g.nx, g.ny, g.nz, g.nxy, xo, yo, zo);
     const size_t self = ((size_t)z * g.ny + y) * g.nx + x;
     Rt l1 = Rt(0);
     if constexpr (kFirst) l1 = (Rt)dldrho[self];
@@ -306,12 +301,7 @@ __global__ void __launch_bounds__(128)
   if (x >= g.nx) return;
   const int y = blockIdx.y, z = blockIdx.z;
   int xo[2 * RR + 1], yo[2 * RR + 1], zo[2 * RR + 1];
-  sfor<0, 2 * RR + 1>([&](auto K) {
-    constexpr int k = decltype(K)::value;
-    xo[k] = wrapi(x - (k - RR), g.nx);
-    yo[k] = wrapi(y - (k - RR), g.ny) * g.nx;
-    if constexpr (D == 3) zo[k] = wrapi(z - (k - RR), g.nz) * g.nxy; else zo[k] = 0;
-  });
+  neighbour_offsets<D, RR>(x, y, z, g.nx, g.ny, g.nz, g.nxy, xo, yo, zo);
   const size_t self = ((size_t)z * g.ny + y) * g.nx + x;
   const size_t n = (size_t)g.ncell;
   const double rho = fields[self];

@@ -493,6 +493,29 @@ __device__ __forceinline__ int wrap1(int v, int n) {
   return v;
 }
 
+// Row offsets of the periodic neighbours x - k, y - k, z - k for k in [-R, R]
+// (index k + R): one correction each way when every extent is at least the reach,
+// a true modulo otherwise (grids smaller than the reach are legal).
+template <int D, int RR>
+__device__ __forceinline__ void neighbour_offsets(int x, int y, int z, int nx, int ny, int nz,
+                                                  int nxy, int* xo, int* yo, int* zo) {
+  if (nx >= RR && ny >= RR && (D == 2 || nz >= RR)) {
+    sfor<0, 2 * RR + 1>([&](auto K) {
+      constexpr int k = decltype(K)::value;
+      xo[k] = wrap1(x - (k - RR), nx);
+      yo[k] = wrap1(y - (k - RR), ny) * nx;
+      if constexpr (D == 3) zo[k] = wrap1(z - (k - RR), nz) * nxy; else zo[k] = 0;
+    });
+  } else {
+    sfor<0, 2 * RR + 1>([&](auto K) {
+      constexpr int k = decltype(K)::value;
+      xo[k] = wrapi(x - (k - RR), nx);
+      yo[k] = wrapi(y - (k - RR), ny) * nx;
+      if constexpr (D == 3) zo[k] = wrapi(z - (k - RR), nz) * nxy; else zo[k] = 0;
+    });
+  }
+}
+
 // Direct-gather kernel: one thread per cell, x fastest across the block,
 // blockIdx.y / z give the row; Q loads per thread straight from HBM / L2.
 // LBM_DIRECT_MINB: resident 128-thread blocks per SM the register budget is cut
@@ -527,21 +550,7 @@ __global__ void __launch_bounds__(128, DirectMinBlocks<S>::value)
   if (x >= g.nx) return;
   const int y = blockIdx.y, z = blockIdx.z;
   int xo[2 * RR + 1], yo[2 * RR + 1], zo[2 * RR + 1];
-  if (g.nx >= RR && g.ny >= RR && g.nz >= RR) {
-    sfor<0, 2 * RR + 1>([&](auto K) {
-      constexpr int k = decltype(K)::value;
-      xo[k] = wrap1(x - (k - RR), g.nx);
-      yo[k] = wrap1(y - (k - RR), g.ny) * g.nx;
-      if constexpr (D == 3) zo[k] = wrap1(z - (k - RR), g.nz) * g.nxy; else zo[k] = 0;
-    });
-  } else {
-    sfor<0, 2 * RR + 1>([&](auto K) {
-      constexpr int k = decltype(K)::value;
-      xo[k] = wrapi(x - (k - RR), g.nx);
-      yo[k] = wrapi(y - (k - RR), g.ny) * g.nx;
-      if constexpr (D == 3) zo[k] = wrapi(z - (k - RR), g.nz) * g.nxy; else zo[k] = 0;
-    });
-  }
+  neighbour_offsets<D, RR>(x, y, z, g.nx, g.ny, g.nz, g.nxy, xo, yo, zo);
   const size_t self = ((size_t)z * g.ny + y) * g.nx + x;
   cell_update<M, S>(
       [&](auto I) {
@@ -617,21 +626,7 @@ __global__ void __launch_bounds__(kSplitThreads, LBM_SPLIT_MINB)
   const int y = blockIdx.y, z = blockIdx.z;
   int xo[2 * RR + 1], yo[2 * RR + 1], zo[2 * RR + 1];
   const int xa = active ? x : xw;
-  if (g.nx >= RR && g.ny >= RR && g.nz >= RR) {
-    sfor<0, 2 * RR + 1>([&](auto K) {
-      constexpr int k = decltype(K)::value;
-      xo[k] = wrap1(xa - (k - RR), g.nx);
-      yo[k] = wrap1(y - (k - RR), g.ny) * g.nx;
-      if constexpr (D == 3) zo[k] = wrap1(z - (k - RR), g.nz) * g.nxy; else zo[k] = 0;
-    });
-  } else {
-    sfor<0, 2 * RR + 1>([&](auto K) {
-      constexpr int k = decltype(K)::value;
-      xo[k] = wrapi(xa - (k - RR), g.nx);
-      yo[k] = wrapi(y - (k - RR), g.ny) * g.nx;
-      if constexpr (D == 3) zo[k] = wrapi(z - (k - RR), g.nz) * g.nxy; else zo[k] = 0;
-    });
-  }
+  neighbour_offsets<D, RR>(xa, y, z, g.nx, g.ny, g.nz, g.nxy, xo, yo, zo);
   const size_t self = ((size_t)z * g.ny + y) * g.nx + xa;
   auto ld = [&](auto I) {
     constexpr int i = decltype(I)::value;
