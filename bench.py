@@ -51,7 +51,7 @@ def parse_args(argv=None):
     p.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16", "fp64"])
     p.add_argument("--grid", default="128x64x64", help="NXxNYxNZ of the D3Q95 Riemann workload")
     p.add_argument("--no-extras", action="store_true", help="skip the forms / adjoint / cpu legs")
-    p.add_argument("--leg", default=None, choices=["forms", "adjoint", "large", "moments"],
+    p.add_argument("--leg", default=None, choices=["forms", "adjoint", "large", "moments", "d2q33"],
                    help="run one secondary leg alone (for profiling) and print its JSON")
     return p.parse_args(argv)
 
@@ -209,7 +209,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     if args.leg:
         fn = {"forms": forms_leg, "adjoint": adjoint_leg, "large": large_leg,
-              "moments": moments_leg}[args.leg]
+              "moments": moments_leg, "d2q33": d2q33_leg}[args.leg]
         if rank == 0:
             print(json.dumps({"leg": args.leg, "result": fn(lbm, W, stream)}), flush=True)
         return
@@ -283,6 +283,7 @@ def run_ours(args):
         line["moments"] = moments_leg(lbm, W, stream, lat=lat, wl=wl)
         line["e2e"] = e2e_leg(lbm, W, wl, fields, args.steps, stream)
         line["forms"] = forms_leg(lbm, W, stream)
+        line["d2q33"] = d2q33_leg(lbm, W, stream)
         line["adjoint"] = adjoint_leg(lbm, W, stream)
         line["large"] = large_leg(lbm, W, stream)
         line["cpu_baseline"] = cpu_baseline_leg()
@@ -359,6 +360,28 @@ def moments_leg(lbm, W, stream, lat=None, wl=None, calls=200):
             "mcells_per_s": round(wl.cells / per_call / 1e6, 1),
             "algorithmic_bytes_per_call": alg, "gbs": round(gbs, 1),
             "frac_of_measured_hbm": round(gbs / peak, 4)}
+
+
+def d2q33_leg(lbm, W, stream, steps=300):
+    """The 2D model on a grid larger than L2 (4096 x 2048, the D2Q33 workload's
+    states, omega 1.5): FP32 and FP16 MLUPS and fraction of the HBM roofline."""
+    import torch
+    peak, _ = hbm_peak()
+    out = {"grid": "4096x2048", "steps": steps}
+    for st in ("fp32", "fp16"):
+        fields = W.riemann_planar(2, 4096, 2048, 1, 2048, (1.0, 1.0), (0.5, 0.8), seed=1)
+        lat = lbm.Lattice("D2Q33", (4096, 2048, 1), 1.5, st)
+        lbm.lbm_set_graph_steps(lat.ctx, GRAPH_STEPS)
+        lat.init(fields.rho, fields.U, fields.theta * lat.info["T0"])
+        dt = time_steps(lbm, lat, steps, 5, stream)
+        cells = 4096 * 2048
+        gbs = cells * 2 * 33 * BYTES[st] / (dt / steps) / 1e9
+        out[st] = {"mlups": round(cells * steps / dt / 1e6, 1), "gbs": round(gbs, 1),
+                   "frac_of_measured_hbm": round(gbs / peak, 4)}
+        lat.close()
+        del fields
+        torch.cuda.empty_cache()
+    return out
 
 
 def forms_leg(lbm, W, stream, steps=200):

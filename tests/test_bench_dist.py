@@ -53,7 +53,7 @@ def test_bench_cli_and_legs_are_wired():
     a = bench.parse_args(["--steps", "7", "--warmup", "3", "--leg", "adjoint", "--storage", "fp16",
                           "--grid", "32x8x8"])
     assert (a.steps, a.warmup, a.leg, a.storage, a.grid) == (7, 3, "adjoint", "fp16", "32x8x8")
-    for name in ("forms_leg", "adjoint_leg", "large_leg", "moments_leg", "e2e_leg", "cpu_baseline_leg",
+    for name in ("forms_leg", "adjoint_leg", "large_leg", "moments_leg", "d2q33_leg", "e2e_leg", "cpu_baseline_leg",
                  "run_reference", "run_ours"):
         assert callable(getattr(bench, name)), name
     assert len(bench.kernel_source_hash()) == 16
