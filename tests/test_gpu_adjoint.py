@@ -36,7 +36,9 @@ def rel(a, b):
 
 
 @pytest.mark.parametrize("model,dims,n,k", [("D3Q95", (9, 4, 3), 6, 4), ("D2Q33", (10, 3, 1), 7, 3),
-                                            ("D3Q95", (133, 3, 2), 5, 2)])
+                                            ("D3Q95", (133, 3, 2), 5, 2),
+                                            # every extent >= the reach: the one-correction wrap
+                                            ("D3Q95", (11, 6, 5), 4, 2), ("D2Q33", (20, 6, 1), 5, 2)])
 def test_fp64_adjoint_matches_oracle(lbm, model, dims, n, k):
     mdl, rho0, U0, T0, c = setup(model, dims, 1)
     rN, dr, dU, dT, dom, _ = gpu_grads(lbm, model, "fp64", dims, 1.6, n, k, rho0, U0, T0, c)
