@@ -529,9 +529,9 @@ print(json.dumps({"steps": n, "seconds": dt, "cells": wl.cells}))
 """
 
 
-def run_oracle_sample(ny, nz, max_steps, budget_s, warmup=1):
+def run_oracle_sample(ny, nz, max_steps, budget_s, warmup=1, threads=None):
     env = dict(os.environ)
-    cores = os.cpu_count() or 1
+    cores = threads or os.cpu_count() or 1
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = str(cores)
     code = CPU_SAMPLE % (ROOT, ny, nz, warmup, max_steps, budget_s)
@@ -546,10 +546,15 @@ def run_oracle_sample(ny, nz, max_steps, budget_s, warmup=1):
 
 def cpu_baseline_leg():
     res = run_oracle_sample(32, 16, 10 ** 9, 15.0)
+    one = run_oracle_sample(32, 16, 10 ** 9, 8.0, threads=1)
     return {"value": round(res["cells"] * res["steps"] / res["seconds"] / 1e6, 4), "unit": "MLUPS",
             "cores": res["cores"], "kind": "oracle",
             "sample": "FP64 numpy oracle, D3Q95 planar Riemann 128x32x16 sub-box (same setup), "
-                      "%d steps in %.1f s, BLAS threads = cores" % (res["steps"], res["seconds"])}
+                      "%d steps in %.1f s, BLAS threads = cores" % (res["steps"], res["seconds"]),
+            "single_thread": {"value": round(one["cells"] * one["steps"] / one["seconds"] / 1e6, 4),
+                              "unit": "MLUPS", "cores": 1,
+                              "sample": "same sub-box, %d steps in %.1f s, one BLAS thread"
+                                        % (one["steps"], one["seconds"])}}
 
 
 # ------------------------------------------------------------------ reference arm (the oracle)
