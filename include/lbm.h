@@ -61,8 +61,10 @@ extern "C" {
 /* Every form stores the deviation h_i = f_i / w_i - 1 from the rest state
  * (rho0 = 1, U = 0, T = T0, where f_i^eq = w_i exactly), so all directions
  * share one dynamic range.  In the FP32 / FP16 / BF16 forms the moment sums for
- * density and energy are Kahan-compensated FP32 and the temperature
- * theta = (E / rho - |u|^2) / D is recovered in FP64. */
+ * density and energy are Kahan-compensated FP32; the temperature
+ * theta = (E / rho - |u|^2) / D is recovered in double-float (hi + lo FP32
+ * pairs, as accurate as an FP64 recovery rounded to FP32) in the FP32 form and
+ * in FP32 in the FP16 / BF16 forms. */
 
 #define LBM_HOST   0
 #define LBM_DEVICE 1

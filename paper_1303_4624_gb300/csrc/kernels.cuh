@@ -190,12 +190,14 @@ __device__ __forceinline__ R edot(R vx, R vy, R vz) {
 //                 (the rest-state moments sum w = 1, sum w xi = 0, sum w |xi|^2 = D are
 //                 exact); opposite pairs are summed first; the rho and E sums are
 //                 Kahan-compensated in FP32
-// a4 temperature  theta - 1 = ((E - D rho) / rho - |u|^2) / D: the energy ratio and the
-//                 subtraction of the kinetic part are done in FP64 (FP64 reciprocal of rho
-//                 from the FP32 estimate by one step of Newton's method for 1/rho,
-//                 r' = r + r (1 - rho r), which squares the estimate's relative error)
+// a4 temperature  theta - 1 = ((E - D rho) / rho - |u|^2) / D: in double-float on the
+//                 FP32 pipe for the FP32 form (rho - 1, E - D rho and 1/rho carried as
+//                 hi + lo pairs; one Newton step r' = r + r (1 - rho r) refines the FP32
+//                 estimate of 1/rho), in FP32 for the FP16 / BF16 forms, in FP64 for the
+//                 FP64 form (cell_state)
 // a5 equilibrium  per group A0, A1, A2; per pair the even / odd parts in s
-// a6 BGK          h_i' = (1 - omega) h_i + omega (rho P_i - 1), handed to the store functor
+// a6 BGK          h_i' = h_i + omega (h_i^eq - h_i) with h_i^eq = rho P_i - 1 (see
+//                 half_collide for the two algebraic forms), handed to the store functor
 // Partial moments of one half of the directions (rest + pairs [P0, P1) when REST).
 // Every kernel forms the moments as the same two halves, first [0, NP/2) with the
 // rest direction, then [NP/2, NP), combined in that order, so that the direct,
@@ -853,10 +855,11 @@ __global__ void __launch_bounds__(256)
   });
 }
 
-// ----------------------------------------------------------------- moments + audit (FP64)
+// ----------------------------------------------------------------- moments + audit
 // Per cell rho = sum f, rho U = sum f e, D rho T = sum f |e|^2 - rho |U|^2 (lattice
-// units), f_i = w_i (1 + h_i).  Each block also writes 8 FP64 audit partials:
-// mass, momentum (3), energy, min f/w, non-finite count, cells.
+// units), f_i = w_i (1 + h_i), written as FP64.  Each block also writes 8 FP64 audit
+// partials: mass, momentum (3), energy, min f/w, non-finite count, cells.  The FP64
+// form sums in FP64 (k_moments below); the other forms use moments_fp32_forms.
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
