@@ -49,6 +49,7 @@ extern "C" {
 #define LBM_EUNSTABLE -4   /* the audit found non-finite populations                */
 #define LBM_ESTATE    -5   /* call out of order (e.g. lbm_step before lbm_init)      */
 #define LBM_EDEVICE   -6   /* a kernel gave up on a bounded wait (reported by sync)  */
+#define LBM_EIO       -7   /* a checkpoint file could not be read or written         */
 
 /* ---- models and storage forms ---- */
 #define LBM_D2Q33 0        /* Table 2: 33 velocities, 8 groups, reach 4 */
@@ -197,6 +198,31 @@ int64_t lbm_steps_done(const lbm_ctx* ctx);
  * Errors: LBM_ESTATE, LBM_EINVAL, LBM_ECUDA.
  */
 int lbm_moments(lbm_ctx* ctx, double* rho, double* U, double* T, int where);
+
+/*
+ * lbm_set_audit_every - failure detection in the time loop: with k > 0, lbm_step
+ * runs the conservation audit (lbm_audit) whenever the step count reaches a
+ * multiple of k (one blocking read-back each time) and stops with
+ * LBM_EUNSTABLE as soon as a population is non-finite; the steps done so far
+ * stay done (lbm_steps_done) and the state is kept for inspection.  k = 0 (the
+ * default) audits nothing.  Errors: LBM_EINVAL.
+ */
+int lbm_set_audit_every(lbm_ctx* ctx, int64_t k);
+
+/*
+ * lbm_save / lbm_load - checkpoint and resume.  lbm_save writes a header (magic
+ * "LBMSTATE", version 1, model, storage, Q, element size, Nx, Ny, Nz, omega, step
+ * count; little-endian as the host writes it) followed by the stored deviations
+ * exactly as lbm_get_raw returns them.  lbm_load reads such a file into a context
+ * of the same model, storage and grid, restores omega and the step count, and
+ * continues bit for bit as the saved run would have.  Blocking; the state moves
+ * through host memory in 64 MiB pieces.  The initial fields of a recorded rollout
+ * are not part of the file (lbm_load invalidates a recording).
+ * Errors: LBM_EINVAL (NULL, foreign or mismatched file), LBM_ESTATE (save before
+ * init), LBM_EIO (open, short read or write), LBM_ECUDA.
+ */
+int lbm_save(lbm_ctx* ctx, const char* path);
+int lbm_load(lbm_ctx* ctx, const char* path);
 
 /*
  * lbm_audit - conservation audit of the current state, deterministic (fixed

@@ -5,6 +5,7 @@
 // ping-pong population buffers, argument validation and the launch sequences.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -353,6 +354,8 @@ struct lbm_ctx {
   int graph_steps = kGraphSteps;   // 0: launch every step directly
   StepGraph graph;
   cudaStream_t cap_stream = nullptr;
+  int64_t audit_every = 0;         // lbm_step audits after every multiple of this many steps
+  double audit_host[kAuditSlots] = {0};
 };
 
 namespace {
@@ -483,6 +486,7 @@ const char* lbm_strerror(int code) {
     case LBM_EUNSTABLE: return "non-finite populations";
     case LBM_ESTATE: return "call out of order";
     case LBM_EDEVICE: return "device-side timeout";
+    case LBM_EIO: return "file I/O failed";
     default: return "unknown error";
   }
 }
@@ -704,12 +708,138 @@ int lbm_init(lbm_ctx* c, const double* rho, const double* U, const double* T, in
   return LBM_OK;
 }
 
+// The conservation audit of the current state into c->audit_host (blocking).
+int run_audit(lbm_ctx* c) {
+  cudaError_t e = c->ops->moments(c->model, c->state[c->cur].p, c->g, nullptr, nullptr, nullptr,
+                                  static_cast<double*>(c->partials.p), c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "audit launch");
+  e = launch_audit_reduce(static_cast<double*>(c->partials.p), moment_blocks(c->g.ncell),
+                          static_cast<double*>(c->audit_out.p), c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "audit reduce launch");
+  c->launches += 2;
+  LBM_CUDA(cudaMemcpyAsync(c->audit_host, c->audit_out.p, kAuditSlots * sizeof(double),
+                           cudaMemcpyDeviceToHost, c->stream));
+  LBM_CUDA(cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
 int lbm_step(lbm_ctx* c, int64_t n) {
   if (!c) return fail(LBM_EINVAL, "ctx is NULL");
   if (!c->inited) return fail(LBM_ESTATE, "lbm_step before lbm_init");
   if (n < 0) return fail(LBM_EINVAL, "n = %lld", (long long)n);
   DeviceGuard dg(c->dev);
-  return do_steps(c, n);
+  if (c->audit_every <= 0) return do_steps(c, n);
+  for (int64_t left = n; left > 0;) {
+    const int64_t m = std::min(left, c->audit_every - c->steps % c->audit_every);
+    int rc = do_steps(c, m);
+    if (rc) return rc;
+    left -= m;
+    if (c->steps % c->audit_every == 0) {
+      if ((rc = run_audit(c))) return rc;
+      if (c->audit_host[6] > 0)   // slot 6: number of non-finite populations
+        return fail(LBM_EUNSTABLE, "%g non-finite populations after step %lld; stepping stopped",
+                    c->audit_host[6], (long long)c->steps);
+    }
+  }
+  return LBM_OK;
+}
+
+int lbm_set_audit_every(lbm_ctx* c, int64_t k) {
+  if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+  if (k < 0) return fail(LBM_EINVAL, "k = %lld", (long long)k);
+  c->audit_every = k;
+  return LBM_OK;
+}
+
+// ---------------------------------------------------------------- checkpoint files
+namespace {
+struct StateFileHeader {
+  char magic[8];
+  int32_t version, model, storage, Q, elem_bytes, reserved;
+  int64_t dims[3];
+  double omega;
+  int64_t steps;
+};
+constexpr char kStateMagic[8] = {'L', 'B', 'M', 'S', 'T', 'A', 'T', 'E'};
+constexpr size_t kFileChunk = (size_t)64 << 20;
+}  // namespace
+
+int lbm_save(lbm_ctx* c, const char* path) {
+  if (!c || !path) return fail(LBM_EINVAL, "ctx or path is NULL");
+  if (!c->inited) return fail(LBM_ESTATE, "lbm_save before lbm_init");
+  DeviceGuard dg(c->dev);
+  StateFileHeader h{};
+  std::memcpy(h.magic, kStateMagic, sizeof h.magic);
+  h.version = 1;
+  h.model = c->model;
+  h.storage = c->storage;
+  h.Q = c->Q;
+  h.elem_bytes = c->ops->elem_bytes;
+  h.dims[0] = c->g.nx;
+  h.dims[1] = c->g.ny;
+  h.dims[2] = c->g.nz;
+  h.omega = c->omega;
+  h.steps = c->steps;
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(LBM_EIO, "cannot open %s for writing", path);
+  int rc = LBM_OK;
+  if (std::fwrite(&h, sizeof h, 1, f) != 1) rc = fail(LBM_EIO, "write failed: %s", path);
+  std::vector<char> buf;
+  const size_t total = state_bytes(c);
+  const char* src = static_cast<const char*>(c->state[c->cur].p);
+  for (size_t off = 0; rc == LBM_OK && off < total; off += kFileChunk) {
+    const size_t m = std::min(kFileChunk, total - off);
+    buf.resize(m);
+    cudaError_t e = cudaMemcpyAsync(buf.data(), src + off, m, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "state read-back");
+    else if (std::fwrite(buf.data(), 1, m, f) != m) rc = fail(LBM_EIO, "write failed: %s", path);
+  }
+  if (std::fclose(f) != 0 && rc == LBM_OK) rc = fail(LBM_EIO, "close failed: %s", path);
+  return rc;
+}
+
+int lbm_load(lbm_ctx* c, const char* path) {
+  if (!c || !path) return fail(LBM_EINVAL, "ctx or path is NULL");
+  DeviceGuard dg(c->dev);
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(LBM_EIO, "cannot open %s", path);
+  StateFileHeader h{};
+  int rc = LBM_OK;
+  if (std::fread(&h, sizeof h, 1, f) != 1) rc = fail(LBM_EIO, "%s: short header", path);
+  else if (std::memcmp(h.magic, kStateMagic, sizeof h.magic) != 0 || h.version != 1)
+    rc = fail(LBM_EINVAL, "%s is not a state file of this library", path);
+  else if (h.model != c->model || h.storage != c->storage || h.Q != c->Q ||
+           h.elem_bytes != c->ops->elem_bytes || h.dims[0] != c->g.nx || h.dims[1] != c->g.ny ||
+           h.dims[2] != c->g.nz)
+    rc = fail(LBM_EINVAL, "%s holds model %d storage %d grid %lldx%lldx%lld; the context differs",
+              path, h.model, h.storage, (long long)h.dims[0], (long long)h.dims[1],
+              (long long)h.dims[2]);
+  else if (!(h.omega >= 0.0 && h.omega < 2.0) || h.steps < 0)
+    rc = fail(LBM_EINVAL, "%s: bad omega or step count", path);
+  std::vector<char> buf;
+  const size_t total = state_bytes(c);
+  char* dst = static_cast<char*>(c->state[0].p);
+  for (size_t off = 0; rc == LBM_OK && off < total; off += kFileChunk) {
+    const size_t m = std::min(kFileChunk, total - off);
+    buf.resize(m);
+    if (std::fread(buf.data(), 1, m, f) != m) {
+      rc = fail(LBM_EIO, "%s: truncated state", path);
+      break;
+    }
+    cudaError_t e = cudaMemcpyAsync(dst + off, buf.data(), m, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "state upload");
+  }
+  std::fclose(f);
+  if (rc != LBM_OK) return rc;
+  c->cur = 0;
+  c->steps = h.steps;
+  c->omega = h.omega;
+  c->inited = true;
+  c->rec.valid = false;
+  c->graph.reset();
+  return LBM_OK;
 }
 
 int64_t lbm_steps_done(const lbm_ctx* c) { return c ? c->steps : -1; }
@@ -747,16 +877,9 @@ int lbm_audit(lbm_ctx* c, double out[8]) {
   if (!c || !out) return fail(LBM_EINVAL, "ctx or out is NULL");
   if (!c->inited) return fail(LBM_ESTATE, "lbm_audit before lbm_init");
   DeviceGuard dg(c->dev);
-  cudaError_t e = c->ops->moments(c->model, c->state[c->cur].p, c->g, nullptr, nullptr, nullptr,
-                                  static_cast<double*>(c->partials.p), c->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "audit launch");
-  e = launch_audit_reduce(static_cast<double*>(c->partials.p), moment_blocks(c->g.ncell),
-                          static_cast<double*>(c->audit_out.p), c->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "audit reduce launch");
-  c->launches += 2;
-  LBM_CUDA(cudaMemcpyAsync(out, c->audit_out.p, kAuditSlots * sizeof(double),
-                           cudaMemcpyDeviceToHost, c->stream));
-  LBM_CUDA(cudaStreamSynchronize(c->stream));
+  int rc = run_audit(c);
+  if (rc) return rc;
+  std::memcpy(out, c->audit_host, sizeof c->audit_host);
   return out[6] > 0 ? fail(LBM_EUNSTABLE, "%g non-finite populations", out[6]) : LBM_OK;
 }
 

@@ -26,7 +26,8 @@ if not os.path.exists(LIB_PATH):
                       "the LBM library has no CPU fallback")
 _lib = ctypes.CDLL(LIB_PATH)
 
-LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ESTATE, LBM_EDEVICE = 0, -1, -2, -3, -4, -5, -6
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ESTATE, LBM_EDEVICE, LBM_EIO = \
+    0, -1, -2, -3, -4, -5, -6, -7
 VARIANT_AUTO, VARIANT_DIRECT, VARIANT_STAGED, VARIANT_SPLIT = 0, 1, 2, 3
 LBM_D2Q33, LBM_D3Q95 = 0, 1
 LBM_FP64, LBM_FP32, LBM_FP16DEV, LBM_BF16DEV = 0, 1, 2, 3
@@ -42,7 +43,8 @@ ADJ_DTYPE = {LBM_FP64: np.float64, LBM_FP32: np.float32, LBM_FP16DEV: np.float32
 # exported symbols of include/lbm.h
 SYMBOLS = ("lbm_model_info", "lbm_set_allocator", "lbm_create", "lbm_destroy", "lbm_set_omega",
            "lbm_set_variant", "lbm_set_graph_steps", "lbm_set_fixed_ends", "lbm_set_stream",
-           "lbm_init", "lbm_step", "lbm_steps_done", "lbm_moments", "lbm_audit",
+           "lbm_init", "lbm_step", "lbm_steps_done", "lbm_set_audit_every", "lbm_save", "lbm_load",
+           "lbm_moments", "lbm_audit",
            "lbm_get_populations", "lbm_set_populations", "lbm_get_raw", "lbm_set_raw",
            "lbm_record", "lbm_record_bounded", "lbm_backward", "lbm_release_record", "lbm_synchronize",
            "lbm_launch_count", "lbm_audit_noalloc", "lbm_equation_count", "lbm_generate_model",
@@ -65,6 +67,9 @@ _sig = {
     "lbm_init": (_i, [_vp, _vp, _vp, _vp, _i]),
     "lbm_step": (_i, [_vp, _i64]),
     "lbm_steps_done": (_i64, [_vp]),
+    "lbm_set_audit_every": (_i, [_vp, _i64]),
+    "lbm_save": (_i, [_vp, ctypes.c_char_p]),
+    "lbm_load": (_i, [_vp, ctypes.c_char_p]),
     "lbm_moments": (_i, [_vp, _vp, _vp, _vp, _i]),
     "lbm_audit": (_i, [_vp, _vp]),
     "lbm_get_populations": (_i, [_vp, _vp, _i]),
@@ -222,6 +227,19 @@ def lbm_set_omega(ctx, omega):
 
 def lbm_set_variant(ctx, variant):
     _check(_lib.lbm_set_variant(ctx, int(variant)), "lbm_set_variant")
+
+
+def lbm_set_audit_every(ctx, k):
+    """lbm_step audits every k steps and stops with LBM_EUNSTABLE on non-finite values."""
+    _check(_lib.lbm_set_audit_every(ctx, int(k)), "lbm_set_audit_every")
+
+
+def lbm_save(ctx, path):
+    _check(_lib.lbm_save(ctx, os.fsencode(path)), "lbm_save")
+
+
+def lbm_load(ctx, path):
+    _check(_lib.lbm_load(ctx, os.fsencode(path)), "lbm_load")
 
 
 def lbm_set_graph_steps(ctx, steps):
