@@ -429,5 +429,11 @@ class Lattice:
     def audit(self):
         return lbm_audit(self.ctx)
 
+    def save(self, path):
+        lbm_save(self.ctx, path)
+
+    def load(self, path):
+        lbm_load(self.ctx, path)
+
     def synchronize(self):
         lbm_synchronize(self.ctx)
