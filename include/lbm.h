@@ -136,7 +136,8 @@ int lbm_set_omega(lbm_ctx* ctx, double omega);
 int lbm_set_variant(lbm_ctx* ctx, int variant);
 
 /*
- * lbm_set_graph_steps - lbm_step replays runs of `steps` launches from a CUDA
+ * lbm_set_graph_steps (execution control; the paper has no counterpart) -
+ * lbm_step replays runs of `steps` launches from a CUDA
  * graph (captured on a stream the library owns, by this call for both starting
  * buffers and again on the first lbm_step after a change that invalidates them,
  * and launched on the context's stream) whenever
@@ -179,8 +180,11 @@ int lbm_set_stream(lbm_ctx* ctx, void* stream);
 int lbm_init(lbm_ctx* ctx, const double* rho, const double* U, const double* T, int where);
 
 /*
- * lbm_step - advance n >= 0 time steps (one fused stream-collide launch each).
- * Enqueues and returns.  Errors: LBM_ESTATE before lbm_init, LBM_EINVAL, LBM_ECUDA.
+ * lbm_step - advance n >= 0 time steps of the paper's update (the BGK rule stated
+ * before the Maxwellian), one fused stream-collide kernel per step, replayed from
+ * CUDA graphs in runs of lbm_set_graph_steps steps.  Enqueues and returns, except
+ * that with lbm_set_audit_every it blocks at each audit.  Errors: LBM_ESTATE
+ * before lbm_init, LBM_EINVAL, LBM_ECUDA, LBM_EUNSTABLE (audit tripped).
  */
 int lbm_step(lbm_ctx* ctx, int64_t n);
 
@@ -200,7 +204,7 @@ int64_t lbm_steps_done(const lbm_ctx* ctx);
 int lbm_moments(lbm_ctx* ctx, double* rho, double* U, double* T, int where);
 
 /*
- * lbm_set_audit_every - failure detection in the time loop: with k > 0, lbm_step
+ * lbm_set_audit_every (failure detection; the paper has none) - with k > 0, lbm_step
  * runs the conservation audit (lbm_audit) whenever the step count reaches a
  * multiple of k (one blocking read-back each time) and stops with
  * LBM_EUNSTABLE as soon as a population is non-finite; the steps done so far
@@ -210,7 +214,8 @@ int lbm_moments(lbm_ctx* ctx, double* rho, double* U, double* T, int where);
 int lbm_set_audit_every(lbm_ctx* ctx, int64_t k);
 
 /*
- * lbm_save / lbm_load - checkpoint and resume.  lbm_save writes a header (magic
+ * lbm_save / lbm_load - checkpoint and resume (the paper has no counterpart).
+ * lbm_save writes a header (magic
  * "LBMSTATE", version 1, model, storage, Q, element size, Nx, Ny, Nz, omega, step
  * count; little-endian as the host writes it) followed by the stored deviations
  * exactly as lbm_get_raw returns them.  lbm_load reads such a file into a context
