@@ -278,15 +278,6 @@ __device__ __forceinline__ FF ff_add(FF a, FF b) {
   const float h = xadd(s, e);
   return {h, xsub(e, xsub(h, s))};
 }
-__device__ __forceinline__ FF warp_sum_ff(FF v) {
-  for (int o = 16; o > 0; o >>= 1) {
-    FF w;
-    w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
-    w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
-    v = ff_add(v, w);
-  }
-  return v;
-}
 __device__ __forceinline__ double ff_to_double(FF v) { return (double)v.hi + (double)v.lo; }
 
 // Cell state from the two halves.  theta - 1 is recovered in double-float on the
@@ -937,45 +928,44 @@ __device__ __forceinline__ void moments_fp32_forms(const S* __restrict__ src, co
     }
     cnt = 1.f;
   }
-  srd = warp_sum_ff(srd);
-  sed = warp_sum_ff(sed);
-  sjx = warp_sum_ff(sjx);
-  sjy = warp_sum_ff(sjy);
-  sjz = warp_sum_ff(sjz);
-  for (int o = 16; o > 0; o >>= 1) {
-    hmin = fminf(hmin, __shfl_xor_sync(0xffffffffu, hmin, o));
-    bad += __shfl_xor_sync(0xffffffffu, bad, o);
-    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-  }
-  // Across the warps of the block: slot k is summed by lane k of warp 0, in
-  // double-float, warp by warp in order (deterministic).
-  constexpr int NW = kMomentThreads / 32;
-  __shared__ FF sh[NW][kAuditSlots];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) {
-    sh[wid][0] = srd;
-    sh[wid][1] = sjx;
-    sh[wid][2] = sjy;
-    sh[wid][3] = sjz;
-    sh[wid][4] = sed;
-    sh[wid][5] = {hmin, 0.f};
-    sh[wid][6] = {bad, 0.f};
-    sh[wid][7] = {cnt, 0.f};
+  // Block sums: every thread's terms go to shared memory and warp w reduces audit
+  // slot w over the block's cells (lane l takes cells l, l + 32, ..., then a
+  // shuffle tree), double-float for the sums, in a fixed order (deterministic).
+  constexpr int NT = kMomentThreads;
+  static_assert(NT / 32 == kAuditSlots, "one warp per audit slot");
+  __shared__ float shv[2 * kAuditSlots][NT];   // slot k: hi in row 2k, lo in row 2k + 1
+  __shared__ FF res[kAuditSlots];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const FF terms[kAuditSlots] = {srd, sjx, sjy, sjz, sed, {hmin, 0.f}, {bad, 0.f}, {cnt, 0.f}};
+#pragma unroll
+  for (int k = 0; k < kAuditSlots; ++k) {
+    shv[2 * k][tid] = terms[k].hi;
+    shv[2 * k + 1][tid] = terms[k].lo;
   }
   __syncthreads();
-  if (threadIdx.x < kAuditSlots) {
-    const int k = threadIdx.x;
-    FF v = sh[0][k];
-    float n = sh[0][7].hi;
-    for (int w = 1; w < NW; ++w) {
-      if (k == 5) v.hi = fminf(v.hi, sh[w][k].hi);
-      else v = ff_add(v, sh[w][k]);
-      n += sh[w][7].hi;                                  // exact: at most 256
-    }
-    double d = ff_to_double(v);
-    if (k == 0) d += (double)n;                                // mass = n + sum (rho - 1)
-    if (k == 4) d = 0.5 * mc.T0 * ((double)D * (double)n + d); // energy
-    if (k == 5) d = (n > 0.f) ? 1.0 + d : 1e300;               // min f / w over the block
+  const bool is_min = wid == 5;
+  FF v = {shv[2 * wid][lane], shv[2 * wid + 1][lane]};
+  for (int c = lane + 32; c < NT; c += 32) {
+    const FF w = {shv[2 * wid][c], shv[2 * wid + 1][c]};
+    if (is_min) v.hi = fminf(v.hi, w.hi);
+    else v = ff_add(v, w);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    FF w;
+    w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    if (is_min) v.hi = fminf(v.hi, w.hi);
+    else v = ff_add(v, w);
+  }
+  if (lane == 0) res[wid] = v;
+  __syncthreads();
+  if (tid < kAuditSlots) {
+    const int k = tid;
+    const float n = res[7].hi;                                   // exact: at most 256
+    double d = ff_to_double(res[k]);
+    if (k == 0) d += (double)n;                                  // mass = n + sum (rho - 1)
+    if (k == 4) d = 0.5 * mc.T0 * ((double)D * (double)n + d);   // energy
+    if (k == 5) d = (n > 0.f) ? 1.0 + d : 1e300;                 // min f / w over the block
     partials[(size_t)blockIdx.x * kAuditSlots + k] = d;
   }
 }
