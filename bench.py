@@ -217,6 +217,7 @@ def run_ours(args):
     wl, fields = W.d3q95_riemann(nx, ny, nz, storage=args.storage)
     Q = lbm.lbm_model_info(wl.model)["Q"]
     lat = make_lattice(lbm, wl, fields)
+    audit0 = lat.audit()
     launches0 = lbm.lbm_launch_count(lat.ctx)
 
     # ---- timed region: K fused stream-collide launches on the resident state
@@ -277,7 +278,12 @@ def run_ours(args):
                      "launch_ms": round(per_launch * 1e3, 5)},
         "clocks": clk,
         "gpu_launches": int(gpu_launches),
-        "audit_after": {"nonfinite": audit["nonfinite"], "mass": audit["mass"]},
+        "audit_after": {"nonfinite": audit["nonfinite"], "mass": audit["mass"],
+                        "mass_drift_rel": audit["mass"] / audit0["mass"] - 1.0,
+                        "energy_drift_rel": audit["energy"] / audit0["energy"] - 1.0,
+                        "momentum_over_mass": float(max(abs(m) for m in audit["momentum"]))
+                                              / audit["mass"],
+                        "steps": args.warmup + args.steps},
     }
     if rank == 0 and not args.no_extras:
         line["moments"] = moments_leg(lbm, W, stream, lat=lat, wl=wl)
