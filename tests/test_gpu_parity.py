@@ -235,6 +235,45 @@ def test_errors_are_reported_before_launch(lbm):
     assert lbm.lbm_launch_count(lat.ctx) == n0 + 5
 
 
+def test_grid_and_argument_limits(lbm):
+    """Empty, oversized and malformed grids and arguments are refused on the host
+    (nothing is allocated or launched); zero steps is a no-op."""
+    for model, dims in (("D3Q95", (0, 8, 8)), ("D3Q95", (8, -1, 8)), ("D3Q95", (8, 8, 70000)),
+                        ("D3Q95", (65536, 65535, 2)),           # 2^33 cells: past the 2^31 limit
+                        ("D2Q33", (8, 8, 2)), (7, (8, 8, 8))):
+        with pytest.raises(lbm.LbmError) as ei:
+            lbm.Lattice(model, dims, 1.0, "fp32")
+        assert ei.value.code == lbm.LBM_EINVAL, (model, dims)
+    for omega in (-0.1, 2.0, float("nan")):
+        with pytest.raises(lbm.LbmError):
+            lbm.Lattice("D3Q95", (8, 8, 8), omega, "fp32")
+    lat = lbm.Lattice("D3Q95", (8, 8, 8), 1.0, "fp32")
+    rho = np.ones((8, 8, 8))
+    lat.init(rho, np.zeros((3, 8, 8, 8)), rho * lat.info["T0"])
+    before = lat.raw()
+    lat.step(0)
+    assert lbm.lbm_steps_done(lat.ctx) == 0
+    assert np.array_equal(before.view(np.uint8), lat.raw().view(np.uint8))
+    with pytest.raises(lbm.LbmError):
+        lat.step(-1)
+    nan_rho = rho.copy()
+    nan_rho[1, 2, 3] = np.nan
+    with pytest.raises(lbm.LbmError) as ei:
+        lat.init(nan_rho, np.zeros((3, 8, 8, 8)), rho)
+    assert ei.value.code == lbm.LBM_EINVAL
+    lat.close()
+
+
+@pytest.mark.parametrize("omega", [1.0, 1.95])
+def test_d3q95_fp64_full_relaxation_and_near_two(lbm, omega):
+    """omega = 1 (every step lands on the equilibrium of the gathered moments) and
+    omega close to the stability limit 2, against the oracle at the FP64 bar."""
+    dims = (24, 6, 5)
+    fields = W.riemann_planar(3, *dims, 12, (1.0, 1.0), (0.7, 0.85), seed=12)
+    mdl, S, lat = run_both(lbm, "D3Q95", "fp64", fields, omega, 10, dims)
+    compare(mdl, S, lat, TOL["fp64"])
+
+
 @pytest.mark.parametrize("storage", ["fp64", "fp32"])
 def test_staged_kernel_matches_oracle_with_ragged_chunk(lbm, storage):
     """136 x 6 x 5: one full 128-cell chunk and a ragged 8-cell chunk per row, halos
