@@ -76,6 +76,10 @@ extern const StorageOps kOpsFP64, kOpsFP32, kOpsFP16, kOpsBF16;
 constexpr int kVariantDirect = 1;
 constexpr int kVariantStaged = 2;
 constexpr int kVariantSplit = 3;
+// Or-ed into the variant of a direct-kernel step: walk the blocks in reverse order.
+// Alternate steps walk opposite ways, so each step starts on the cells its
+// predecessor wrote last, which are still in L2.
+constexpr int kStepReverse = 0x100;
 inline bool staged_applicable(const Grid& g) { return g.nx % 8 == 0; }
 
 constexpr int kAuditSlots = 8;

@@ -87,6 +87,8 @@ cudaError_t step_staged_m(const void* src, void* dst, const Grid& g, double omeg
 template <int M>
 cudaError_t step_m(const void* src, void* dst, const Grid& g, double omega, int variant, int* status,
                    cudaStream_t st) {
+  const int rev = (variant & kStepReverse) ? 1 : 0;
+  variant &= ~kStepReverse;
   if (variant == kVariantStaged) return step_staged_m<M>(src, dst, g, omega, status, st);
   if constexpr (!std::is_same<S, double>::value) {
     if (variant == kVariantSplit) {
@@ -111,10 +113,10 @@ cudaError_t step_m(const void* src, void* dst, const Grid& g, double omega, int 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k_stream_collide<M, S>, static_cast<const S*>(src),
-                            static_cast<S*>(dst), g, omega);
+                            static_cast<S*>(dst), g, omega, rev);
 #else
   k_stream_collide<M, S><<<grid, bx, 0, st>>>(static_cast<const S*>(src), static_cast<S*>(dst), g,
-                                              omega);
+                                              omega, rev);
 #endif
   return cudaGetLastError();
 }

@@ -379,8 +379,15 @@ int pick_variant(const lbm_ctx* c) {
 // n steps enqueued on stream st starting from buffer *cur (which is advanced).
 cudaError_t enqueue_steps(lbm_ctx* c, int64_t n, int variant, int* cur, cudaStream_t st) {
   for (int64_t k = 0; k < n; ++k) {
+    // steps out of buffer 1 walk the grid backwards (kStepReverse): consecutive steps
+    // alternate direction and each starts on its predecessor's L2-resident output
+#ifndef LBM_NO_REVERSE
+    const int v = variant | ((variant == kVariantDirect && *cur == 1) ? kStepReverse : 0);
+#else
+    const int v = variant;
+#endif
     cudaError_t e = c->ops->step(c->model, c->state[*cur].p, c->state[*cur ^ 1].p, c->g, c->omega,
-                                 variant, static_cast<int*>(c->status.p), st);
+                                 v, static_cast<int*>(c->status.p), st);
     if (e != cudaSuccess) return e;
     *cur ^= 1;
     if (c->fix_width > 0) {
