@@ -112,11 +112,18 @@ cudaError_t step_m(const void* src, void* dst, const Grid& g, double omega, int 
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_stream_collide<M, S>, static_cast<const S*>(src),
-                            static_cast<S*>(dst), g, omega, rev);
+  if (rev)
+    return cudaLaunchKernelEx(&cfg, k_stream_collide<M, S, true>, static_cast<const S*>(src),
+                              static_cast<S*>(dst), g, omega);
+  return cudaLaunchKernelEx(&cfg, k_stream_collide<M, S, false>, static_cast<const S*>(src),
+                            static_cast<S*>(dst), g, omega);
 #else
-  k_stream_collide<M, S><<<grid, bx, 0, st>>>(static_cast<const S*>(src), static_cast<S*>(dst), g,
-                                              omega, rev);
+  if (rev)
+    k_stream_collide<M, S, true><<<grid, bx, 0, st>>>(static_cast<const S*>(src),
+                                                      static_cast<S*>(dst), g, omega);
+  else
+    k_stream_collide<M, S, false><<<grid, bx, 0, st>>>(static_cast<const S*>(src),
+                                                       static_cast<S*>(dst), g, omega);
 #endif
   return cudaGetLastError();
 }

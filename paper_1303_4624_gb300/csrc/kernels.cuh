@@ -532,22 +532,21 @@ __device__ __forceinline__ void allow_next_grid() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-// rev: walk the blocks in reverse order (the block scheduler issues blocks in
+// REV: walk the blocks in reverse order (the block scheduler issues blocks in
 // increasing index order), so that a step following a forward step starts on the
 // cells written last, still resident in L2.
-template <int M, class S>
+template <int M, class S, bool REV>
 __global__ void __launch_bounds__(128, DirectMinBlocks<S>::value)
-    k_stream_collide(const S* __restrict__ src, S* __restrict__ dst, Grid g, double omega,
-                     int rev) {
+    k_stream_collide(const S* __restrict__ src, S* __restrict__ dst, Grid g, double omega) {
   using Mo = Model<M>;
   constexpr int D = Mo::D, RR = Mo::R;
   wait_prior_grid();
   allow_next_grid();
-  const int bx = rev ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x;
+  const int bx = REV ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x;
   const int x = bx * blockDim.x + threadIdx.x;
   if (x >= g.nx) return;
-  const int y = rev ? (int)(gridDim.y - 1 - blockIdx.y) : (int)blockIdx.y;
-  const int z = rev ? (int)(gridDim.z - 1 - blockIdx.z) : (int)blockIdx.z;
+  const int y = REV ? (int)(gridDim.y - 1 - blockIdx.y) : (int)blockIdx.y;
+  const int z = REV ? (int)(gridDim.z - 1 - blockIdx.z) : (int)blockIdx.z;
   int xo[2 * RR + 1], yo[2 * RR + 1], zo[2 * RR + 1];
   neighbour_offsets<D, RR>(x, y, z, g.nx, g.ny, g.nz, g.nxy, xo, yo, zo);
   const size_t self = ((size_t)z * g.ny + y) * g.nx + x;
