@@ -158,11 +158,12 @@ def as_storage(a, storage):
 @pytest.mark.parametrize("storage", ["fp64", "fp32", "fp16", "bf16"])
 @pytest.mark.parametrize("model,dims", [("D3Q95", (37, 6, 7)), ("D3Q95", (2, 3, 4)),
                                         ("D3Q95", (40, 6, 7)), ("D3Q95", (8, 3, 2)),
+                                        ("D3Q95", (133, 4, 3)),
                                         ("D2Q33", (131, 5, 1)), ("D2Q33", (3, 2, 1)),
                                         ("D2Q33", (136, 5, 1)), ("D2Q33", (8, 2, 1))])
 def test_streaming_is_a_bit_exact_permutation(lbm, model, dims, storage):
-    """(Nx % 8 == 0 grids run the staged kernel, the others the direct one.)"""
-    """omega = 0: after n steps h_i(x) = h_i((x - n e_i) mod N) bit for bit."""
+    """omega = 0: after n steps h_i(x) = h_i((x - n e_i) mod N) bit for bit, on grids
+    smaller than the reach, ragged in x, and spanning several 128-cell blocks."""
     lat = lbm.Lattice(model, dims, 0.0, storage)
     Q = lat.info["Q"]
     e = lat.info["e"]
