@@ -511,15 +511,20 @@ __device__ __forceinline__ void neighbour_offsets(int x, int y, int z, int nx, i
 
 // Direct-gather kernel: one thread per cell, x fastest across the block,
 // blockIdx.y / z give the row; Q loads per thread straight from HBM / L2.
-// LBM_DIRECT_MINB: resident 128-thread blocks per SM the register budget is cut
-// for (128 registers at 4: 16 warps per SM; measured best for the FP32 and FP16
-// forms).  The FP64 form keeps 2 (its 95 doubles need 190 registers).
+// LBM_DIRECT_MINB: resident 128-thread blocks per SM the D3Q95 register budget is
+// cut for (128 registers at 4: 16 warps per SM; measured best for the FP32 and
+// FP16 forms).  D2Q33's 33 populations fit fewer registers without spilling, and
+// more resident warps pay: 8 blocks (64 registers) for FP32, 6 (80 registers) for
+// the 16-bit forms (4096 x 2048: +4.6 % and +12.8 % over 4 blocks).  The FP64
+// form keeps 2 (D3Q95's 95 doubles need 190 registers).
 #ifndef LBM_DIRECT_MINB
 #define LBM_DIRECT_MINB 4
 #endif
-template <class S>
+template <int M, class S>
 struct DirectMinBlocks {
-  static constexpr int value = std::is_same<S, double>::value ? 2 : LBM_DIRECT_MINB;
+  static constexpr int value = std::is_same<S, double>::value
+                                   ? 2
+                                   : (Model<M>::Q == 33 ? (sizeof(S) == 4 ? 8 : 6) : LBM_DIRECT_MINB);
 };
 // Launched with programmatic stream serialization: the next step's grid may be
 // scheduled while this one drains; griddepcontrol.wait holds every thread until
@@ -536,7 +541,7 @@ __device__ __forceinline__ void allow_next_grid() {
 // increasing index order), so that a step following a forward step starts on the
 // cells written last, still resident in L2.
 template <int M, class S, bool REV>
-__global__ void __launch_bounds__(128, DirectMinBlocks<S>::value)
+__global__ void __launch_bounds__(128, DirectMinBlocks<M, S>::value)
     k_stream_collide(const S* __restrict__ src, S* __restrict__ dst, Grid g, double omega) {
   using Mo = Model<M>;
   constexpr int D = Mo::D, RR = Mo::R;
