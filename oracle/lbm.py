@@ -156,13 +156,17 @@ def macroscopic(model, S):
 
 def audit(model, S):
     """Global totals in lattice units: mass, momentum [D], energy (sum f |e|^2 / 2),
-    min_i f_i / w_i and the number of non-finite populations."""
+    min_i f_i / w_i and the number of non-finite populations.
+
+    The minimum runs over the numbers among the f_i / w_i (infinities included,
+    NaN skipped: a NaN is reported by the non-finite count, not as a minimum)."""
     f = S.reshape(model.Q, -1)
     e = model.e.astype(np.float64)
-    mass = float(f.sum())
-    mom = (e.T @ f).sum(axis=1)
-    energy = float(0.5 * ((e * e).sum(axis=1) @ f).sum())
-    minratio = float((f / model.w[:, None]).min())
+    with np.errstate(invalid="ignore"):
+        mass = float(f.sum())
+        mom = (e.T @ f).sum(axis=1)
+        energy = float(0.5 * ((e * e).sum(axis=1) @ f).sum())
+    minratio = float(np.fmin.reduce((f / model.w[:, None]).ravel()))
     nonfinite = int((~np.isfinite(f)).sum())
     return {"mass": mass, "momentum": mom, "energy": energy,
             "min_f_over_w": minratio, "nonfinite": nonfinite}

@@ -178,3 +178,56 @@ def test_paper_shock_tube_with_fixed_ends():
     assert abs(th[mR].mean() / (st.p / st.rho_R / T0) - 1) < 5e-3
     fe_lo = lbm.init_populations(mdl, np.full((1, 1, 1), 4.0), np.zeros((3, 1, 1, 1)), np.full((1, 1, 1), T0))
     assert np.array_equal(S[:, :5], np.broadcast_to(fe_lo, (mdl.Q, 5, 1, 1)))
+
+
+@pytest.mark.parametrize("name,shape", [("D2Q33", (1, 5, 7)), ("D3Q95", (3, 4, 5))])
+def test_audit_totals_in_absolute_terms(name, shape):
+    """The audit's totals equal the macroscopic definitions (Formula 1 with n <= 2:
+    density, momentum and energy moments) of the fields the state was built from,
+    in lattice units: mass = sum rho, momentum = sum rho U, energy =
+    sum rho (D T + |U|^2) / 2.  The state is the discrete equilibrium of random
+    fields, whose moments through order 2 are the Maxwellian's (pinned in
+    test_oracle_equilibrium), so the expected totals come from the input fields, not
+    from the populations: a missing 1/2, or momentum or energy taken in the
+    unit-variance variables xi = sqrt(2) c e instead of e, fails."""
+    mdl = get_model(name)
+    rng = np.random.default_rng(31)
+    rho = 1.0 + 0.2 * rng.uniform(-1, 1, shape)
+    U = 0.1 * rng.uniform(-1, 1, (mdl.D,) + shape)
+    T = mdl.T0 * (1.0 + 0.2 * rng.uniform(-1, 1, shape))
+    a = lbm.audit(mdl, lbm.init_populations(mdl, rho, U, T))
+    mass = rho.sum()
+    mom = (rho * U).reshape(mdl.D, -1).sum(axis=1)
+    energy = (0.5 * rho * (mdl.D * T + (U * U).sum(axis=0))).sum()
+    assert abs(a["mass"] - mass) <= 1e-13 * mass
+    assert np.max(np.abs(a["momentum"] - mom)) <= 1e-13 * mass
+    assert abs(a["energy"] - energy) <= 1e-13 * energy
+    assert a["nonfinite"] == 0
+    # the rest state f = w at rho = 1: min f / w is exactly 1
+    rest = lbm.init_populations(mdl, np.ones(shape), np.zeros((mdl.D,) + shape),
+                                np.full(shape, mdl.T0))
+    assert abs(lbm.audit(mdl, rest)["min_f_over_w"] - 1.0) < 1e-14
+
+
+@pytest.mark.parametrize("name", ["D2Q33", "D3Q95"])
+def test_audit_minimum_and_nonfinite_count_on_a_hand_built_state(name):
+    """f_i = 1.5 w_i everywhere except one population of one cell set to 0.125 w_k
+    (k at the end of a symmetry group, so the next direction's weight differs), and
+    a NaN and two infinities planted elsewhere: min f / w is exactly 0.125 with the
+    weights in direction order, the three non-finite values are counted one by one,
+    and NaN never wins the minimum.  A +/- infinity pair would make the minimum
+    -inf, so only +inf is planted here beside the NaN."""
+    mdl = get_model(name)
+    shape = (2, 3, 4) if mdl.D == 3 else (1, 3, 4)
+    S = np.broadcast_to((1.5 * mdl.w).reshape(-1, 1, 1, 1), (mdl.Q,) + shape).copy()
+    # the last direction of the first non-rest group: its weight differs from the next one's
+    k = next(i for i in range(1, mdl.Q - 1) if mdl.w[i] != mdl.w[i + 1])
+    S[k, 0, 1, 2] = 0.125 * mdl.w[k]
+    S[0, 0, 2, 3] = np.nan
+    S[mdl.Q - 1, 0, 0, 0] = np.inf
+    S[1, 0, 2, 1] = np.inf
+    a = lbm.audit(mdl, S)
+    assert a["min_f_over_w"] == 0.125
+    assert a["nonfinite"] == 3
+    S[1, 0, 2, 1] = -np.inf
+    assert lbm.audit(mdl, S)["min_f_over_w"] == -np.inf
