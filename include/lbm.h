@@ -62,10 +62,9 @@ extern "C" {
 /* Every form stores the deviation h_i = f_i / w_i - 1 from the rest state
  * (rho0 = 1, U = 0, T = T0, where f_i^eq = w_i exactly), so all directions
  * share one dynamic range.  In the FP32 / FP16 / BF16 forms the moment sums for
- * density and energy are Kahan-compensated FP32; the temperature
+ * density and energy are Kahan-compensated FP32, and the temperature
  * theta = (E / rho - |u|^2) / D is recovered in double-float (hi + lo FP32
- * pairs, as accurate as an FP64 recovery rounded to FP32) in the FP32 form and
- * in FP32 in the FP16 / BF16 forms. */
+ * pairs, as accurate as an FP64 recovery rounded to FP32) in all three. */
 
 #define LBM_HOST   0
 #define LBM_DEVICE 1
@@ -101,6 +100,10 @@ int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn free_fn, void* user);
 
 /*
  * lbm_create - allocate a context for one periodic grid on the current device.
+ * The model's velocity set and weights are those of Table 2 (D2Q33) or Table 3
+ * (D3Q95), the weights re-solved from Formula 5 as lbm_model_info describes;
+ * omega is the relaxation frequency of the paper's BGK update (the rule stated
+ * before the Maxwellian).
  *   model:   LBM_D2Q33 or LBM_D3Q95
  *   dims:    {Nx, Ny, Nz}, each >= 1, Nz == 1 for D2Q33; Nx*Ny*Nz < 2^31
  *   omega:   BGK relaxation frequency (the paper's omega), 0 <= omega < 2
@@ -169,7 +172,11 @@ int lbm_set_fixed_ends(lbm_ctx* ctx, int axis, int width, const double* lo, cons
 int lbm_set_stream(lbm_ctx* ctx, void* stream);
 
 /*
- * lbm_init - set every cell to the discrete equilibrium f_i^eq(rho, U, T).
+ * lbm_init - set every cell to the discrete equilibrium f_i^eq(rho, U, T): the
+ * fourth-order Hermite expansion of the Maxwellian (the distribution stated after
+ * the update rule) on the model's weights, i.e. Formula 1's moment conditions
+ * with m = N = 4, in the dimensionless variables theta = T / T0, u = c U
+ * defined after the Maxwellian.
  *   rho [cells], U [D][cells] (lattice units), T [cells] (lattice units),
  *   all FP64 in `where` memory.  rho > 0 and T > 0 and all values finite
  *   (checked on the host for LBM_HOST; for LBM_DEVICE inputs the values are
@@ -222,9 +229,13 @@ int lbm_set_audit_every(lbm_ctx* ctx, int64_t k);
  * of the same model, storage and grid, restores omega and the step count, and
  * continues bit for bit as the saved run would have.  Blocking; the state moves
  * through host memory in 64 MiB pieces.  The initial fields of a recorded rollout
- * are not part of the file (lbm_load invalidates a recording).
+ * are not part of the file (lbm_load invalidates a recording).  lbm_load checks
+ * the file's length against the context's state before it uploads anything and
+ * uploads into the spare ping-pong buffer, switching to it only after the last
+ * piece: a refused or failed load leaves the context's state, omega and step
+ * count as they were.
  * Errors: LBM_EINVAL (NULL, foreign or mismatched file), LBM_ESTATE (save before
- * init), LBM_EIO (open, short read or write), LBM_ECUDA.
+ * init), LBM_EIO (open, short read or write, wrong file length), LBM_ECUDA.
  */
 int lbm_save(lbm_ctx* ctx, const char* path);
 int lbm_load(lbm_ctx* ctx, const char* path);
@@ -315,21 +326,29 @@ int64_t lbm_launch_count(const lbm_ctx* ctx);
  * pool that has reserved the GPU) or code in a time loop that cannot take the
  * device-wide synchronisation cudaMalloc / cudaFree may cause.
  *   model, storage, dims: as for lbm_create (the layout lbm_get_raw returns);
- *   h:      device pointer to the stored deviations, Q * cells elements;
- *   out:    device pointer to 8 doubles, filled as lbm_audit's out (no host copy);
+ *   h:      device pointer (current device) to the stored deviations, Q * cells
+ *           elements;
+ *   h_bytes: size of the buffer at h; less than Q * cells * element size is
+ *           refused;
+ *   out:    device pointer (current device) to 8 doubles, filled as lbm_audit's
+ *           out (no host copy);
  *   stream: cudaStream_t the work is ordered on (NULL = legacy default stream).
+ * h and out are checked with cudaPointerGetAttributes (no allocation): host or
+ * another device's memory returns LBM_EINVAL without a launch.
  * The per-block partial sums live in one file-scope device array of 8192 x 8
  * doubles (512 KiB, held by every GPU that loads the library until the process
  * exits), so grids of at most 2,097,152 cells are accepted; larger grids return
  * LBM_EINVAL.  The first call on a device does a set-up with that device
  * current (the array's device address and the constant model tables); make
- * that first call before any stream capture.  All calls share the array:
+ * that first call before any stream capture.  A device reset destroys what the
+ * set-up made; the first call after it repeats the set-up (it is keyed by the
+ * CUDA context's id), so make that call before any capture too.  All calls share the array:
  * calls whose work overlaps on the GPU (other streams, other threads) race.
  * Each call overwrites every partial it reads, so nothing needs clearing.
  * Returns after enqueueing.  Errors: LBM_EINVAL, LBM_ECUDA.
  */
-int lbm_audit_noalloc(int model, int storage, const int64_t dims[3], const void* h, double* out,
-                      void* stream);
+int lbm_audit_noalloc(int model, int storage, const int64_t dims[3], const void* h,
+                      size_t h_bytes, double* out, void* stream);
 
 /*
  * lbm_equation_count - Omega(m, D), the number of moment equations of Formula 5

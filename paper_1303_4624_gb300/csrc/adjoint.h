@@ -67,5 +67,9 @@ int ctx_fail(int code, const char* msg);
 int ctx_cuda_fail(cudaError_t e, const char* what);
 const ModelConst* ctx_model_const(int model);
 CtxView ctx_view(lbm_ctx* c);
+// Unique id of the CUDA context current on the calling thread (0 if none is current
+// or the driver cannot tell).  A device reset destroys the primary context, and the
+// next one has a new id: per-device set-up keyed by this id is redone after a reset.
+unsigned long long current_context_id();
 
 }  // namespace lbm

@@ -35,35 +35,53 @@ static __device__ __align__(256) double g_audit_scratch[kNoAllocMaxBlocks * kAud
 
 struct DeviceSetup {
   int dev;
-  double* scratch;   // device address of g_audit_scratch on `dev`
+  unsigned long long ctx_id;   // the context the set-up was made in (0: unknown)
+  double* scratch;             // device address of g_audit_scratch on `dev`
 };
 std::mutex g_mu;
 std::vector<DeviceSetup> g_setup;
 
-// Once per device, with that device current: the scratch address and this
-// translation unit's copy of the constant-memory model tables.
+// Once per device and context, with that device current: the scratch address and
+// this translation unit's copy of the constant-memory model tables.  Keyed by the
+// context's id as well as the device, so that a device reset (which destroys the
+// context, its module and its constant memory) leads to a fresh set-up.
 int setup_current_device(double** scratch) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return ctx_cuda_fail(e, "cudaGetDevice");
   std::lock_guard<std::mutex> lk(g_mu);
+  const unsigned long long id = current_context_id();
   for (const auto& s : g_setup)
-    if (s.dev == dev) {
+    if (s.dev == dev && s.ctx_id == id) {
       *scratch = s.scratch;
       return LBM_OK;
     }
+  void* p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_audit_scratch);   // also makes the primary context current
+  if (e != cudaSuccess) return ctx_cuda_fail(e, "cudaGetSymbolAddress(g_audit_scratch)");
   const ModelConst* m0 = ctx_model_const(0);
   const ModelConst* m1 = ctx_model_const(1);
   if (!m0 || !m1) return ctx_fail(LBM_EINVAL, "model table solve failed");
   ModelConst both[2] = {*m0, *m1};
   e = cudaMemcpyToSymbol(c_mc, both, sizeof both);
   if (e != cudaSuccess) return ctx_cuda_fail(e, "constant table upload");
-  void* p = nullptr;
-  e = cudaGetSymbolAddress(&p, g_audit_scratch);
-  if (e != cudaSuccess) return ctx_cuda_fail(e, "cudaGetSymbolAddress(g_audit_scratch)");
-  g_setup.push_back({dev, static_cast<double*>(p)});
+  const unsigned long long now = current_context_id();
+  for (auto it = g_setup.begin(); it != g_setup.end();)
+    it = (it->dev == dev) ? g_setup.erase(it) : it + 1;
+  g_setup.push_back({dev, now, static_cast<double*>(p)});
   *scratch = static_cast<double*>(p);
   return LBM_OK;
+}
+
+// True when p is device (or managed) memory of device `dev`.  Asks the driver
+// about the pointer; allocates nothing.
+bool is_device_pointer(const void* p, int dev) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
 template <class S>
@@ -85,7 +103,7 @@ cudaError_t launch(int model, const void* h, const Grid& g, double* scratch, dou
 }  // namespace
 
 extern "C" int lbm_audit_noalloc(int model, int storage, const int64_t dims[3], const void* h,
-                                 double* out, void* stream) {
+                                 size_t h_bytes, double* out, void* stream) {
   if (model != LBM_D2Q33 && model != LBM_D3Q95) return ctx_fail(LBM_EINVAL, "unknown model");
   if (storage < LBM_FP64 || storage > LBM_BF16DEV) return ctx_fail(LBM_EINVAL, "unknown storage");
   if (!dims || !h || !out) return ctx_fail(LBM_EINVAL, "dims, h and out are required");
@@ -100,9 +118,21 @@ extern "C" int lbm_audit_noalloc(int model, int storage, const int64_t dims[3], 
              kNoAllocMaxBlocks * kMomentThreads, ncell);
     return ctx_fail(LBM_EINVAL, msg);
   }
+  const size_t esize = storage == LBM_FP64 ? 8 : (storage == LBM_FP32 ? 4 : 2);
+  const size_t need = (size_t)(model == LBM_D2Q33 ? Model<0>::Q : Model<1>::Q) * (size_t)ncell * esize;
+  if (h_bytes < need) {
+    char msg[160];
+    snprintf(msg, sizeof msg, "h holds %zu bytes; the grid's populations need %zu", h_bytes, need);
+    return ctx_fail(LBM_EINVAL, msg);
+  }
   double* scratch = nullptr;
   int rc = setup_current_device(&scratch);
   if (rc) return rc;
+  int dev = 0;
+  cudaError_t de = cudaGetDevice(&dev);
+  if (de != cudaSuccess) return ctx_cuda_fail(de, "cudaGetDevice");
+  if (!is_device_pointer(h, dev) || !is_device_pointer(out, dev))
+    return ctx_fail(LBM_EINVAL, "h and out must be device memory of the current device");
   Grid g;
   g.nx = (int)dims[0];
   g.ny = (int)dims[1];

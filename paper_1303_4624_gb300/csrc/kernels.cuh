@@ -191,10 +191,10 @@ __device__ __forceinline__ R edot(R vx, R vy, R vz) {
 //                 exact); opposite pairs are summed first; the rho and E sums are
 //                 Kahan-compensated in FP32
 // a4 temperature  theta - 1 = ((E - D rho) / rho - |u|^2) / D: in double-float on the
-//                 FP32 pipe for the FP32 form (rho - 1, E - D rho and 1/rho carried as
-//                 hi + lo pairs; one Newton step r' = r + r (1 - rho r) refines the FP32
-//                 estimate of 1/rho), in FP32 for the FP16 / BF16 forms, in FP64 for the
-//                 FP64 form (cell_state)
+//                 FP32 pipe for the FP32, FP16 and BF16 forms (rho - 1, E - D rho and
+//                 1/rho carried as hi + lo pairs; one Newton step r' = r + r (1 - rho r)
+//                 refines the FP32 estimate of 1/rho), in FP64 for the FP64 form
+//                 (cell_state)
 // a5 equilibrium  per group A0, A1, A2; per pair the even / odd parts in s
 // a6 BGK          h_i' = h_i + omega (h_i^eq - h_i) with h_i^eq = rho P_i - 1 (see
 //                 half_collide for the two algebraic forms), handed to the store functor
@@ -281,8 +281,10 @@ __device__ __forceinline__ FF ff_add(FF a, FF b) {
 __device__ __forceinline__ double ff_to_double(FF v) { return (double)v.hi + (double)v.lo; }
 
 // Cell state from the two halves.  theta - 1 is recovered in double-float on the
-// FP32 pipe for the FP32 form (F64 = true, Rt = float), in FP32 for the FP16 / BF16
-// forms (F64 = false) and in FP64 for the FP64 form (Rt = double).
+// FP32 pipe for the FP32-arithmetic forms (Rt = float: FP32, FP16 and BF16 storage)
+// and in FP64 for the FP64 form (Rt = double).  The energy difference E - D rho
+// cancels badly where the gas is hot and dense (behind a shock), so it is formed
+// with FP64-grade precision in every form, whatever the storage rounding.
 template <class Rt>
 struct CellState {
   Rt q, t, uax, uay, uaz;   // |u|^2, theta - 1, a u
@@ -290,41 +292,14 @@ struct CellState {
   Rt wr, wrd;               // omega rho, omega (rho - 1)
 };
 
-template <int M, class Rt, bool F64 = true>
+template <int M, class Rt>
 __device__ __forceinline__ CellState<Rt> cell_state(const HalfMoments<Rt>& A,
                                                     const HalfMoments<Rt>& B, double omega) {
   constexpr int D = Model<M>::D;
   const ModelConst& mc = c_mc[M];
   CellState<Rt> c;
-  if constexpr (std::is_same<Rt, float>::value && !F64) {
-    // FP16 / BF16 forms: the stored deviations carry a relative rounding of 2^-11
-    // (2^-8 for BF16); the FP32 rounding of the compensated sums (2^-24) is far
-    // below it, so the whole recovery runs on the FP32 pipe.
-    const float rd = xadd(xsub(A.rs, A.rc), xsub(B.rs, B.rc));
-    const float ed = xadd(xsub(A.es, A.ec), xsub(B.es, B.ec));
-    const float jx = xadd(A.jx, B.jx), jy = xadd(A.jy, B.jy), jz = xadd(A.jz, B.jz);
-    const float rho = xadd(1.0f, rd);
-    const float r0 = __fdividef(1.0f, rho);
-    const float ir = xfma(r0, xfma(-rho, r0, 1.0f), r0);   // one Newton step for 1/rho
-    const float a = gA<float>(mc);
-    const float ux = xmul(xmul(a, jx), ir), uy = xmul(xmul(a, jy), ir);
-    const float uz = (D == 3) ? xmul(xmul(a, jz), ir) : 0.0f;
-    c.q = xfma(ux, ux, xfma(uy, uy, xmul(uz, uz)));
-    const float v = xfma(xfma(-(float)D, rd, ed), ir, -c.q);
-    const float y = xmul(v, cst<float>(1.0 / D));
-    c.t = xfma(xfma(-(float)D, y, v), cst<float>(1.0 / D), y);   // unbiased v / D
-    c.uax = xmul(a, ux);
-    c.uay = xmul(a, uy);
-    c.uaz = xmul(a, uz);
-    c.rho = rho;
-    c.rdev = rd;
-    const float om = cst<float>(omega);
-    c.wr = xmul(om, rho);
-    c.wrd = xmul(om, rd);
-    return c;
-  }
   if constexpr (std::is_same<Rt, float>::value) {
-    // FP32 form: rho - 1 and E - D rho as double-float on the FP32 pipe
+    // FP32-arithmetic forms: rho - 1 and E - D rho as double-float on the FP32 pipe
     FF rd, ed, rho;
     two_sum(A.rs, B.rs, rd.hi, rd.lo);
     rd.lo = xsub(rd.lo, xadd(A.rc, B.rc));
@@ -457,7 +432,6 @@ template <class S>
 struct FormOpts {
   static constexpr bool kShell = sizeof(S) == 2;
   static constexpr bool kExact = sizeof(S) >= 4;
-  static constexpr bool kF64Theta = sizeof(S) >= 4;
 };
 
 template <int M, class S, class Load, class Store>
@@ -473,7 +447,7 @@ __device__ __forceinline__ void cell_update(Load&& ld, double omega, Store&& st)
   // a3, a4
   const HalfMoments<Rt> A = half_moments<M, Rt, 0, NH, true, SH>(hv);
   const HalfMoments<Rt> B = half_moments<M, Rt, NH, NP, false, SH>(hv);
-  const CellState<Rt> c = cell_state<M, Rt, FormOpts<S>::kF64Theta>(A, B, omega);
+  const CellState<Rt> c = cell_state<M, Rt>(A, B, omega);
   // a5, a6
   half_collide<M, Rt, 0, NH, true, EX>(c, omega, hv, st);
   half_collide<M, Rt, NH, NP, false, EX>(c, omega, hv, st);
@@ -610,7 +584,7 @@ __device__ __forceinline__ void half_update(Load&& ld, double omega, Store&& st,
   const float* b = &xch[pair][1][0][lane];
   A.rs = a[0]; A.rc = a[32]; A.es = a[64]; A.ec = a[96]; A.jx = a[128]; A.jy = a[160]; A.jz = a[192];
   B.rs = b[0]; B.rc = b[32]; B.es = b[64]; B.ec = b[96]; B.jx = b[128]; B.jy = b[160]; B.jz = b[192];
-  const CellState<Rt> c = cell_state<M, Rt, FormOpts<S>::kF64Theta>(A, B, omega);
+  const CellState<Rt> c = cell_state<M, Rt>(A, B, omega);
   half_collide<M, Rt, P0, P1, HALF == 0, FormOpts<S>::kExact>(c, omega, hv, st);
 }
 

@@ -3,6 +3,7 @@
 // Holds the model tables (velocity sets expanded at compile time in
 // velset.cuh, weights solved here from Formula 5), the context object with its
 // ping-pong population buffers, argument validation and the launch sequences.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -218,7 +219,8 @@ bool build_host_model(int model, HostModel* hm) {
 std::mutex g_model_mu;
 HostModel g_models[2];
 bool g_model_ok[2] = {false, false};
-std::vector<int> g_uploaded;  // devices whose constant tables are current
+// (device, context id) pairs whose constant tables are current
+std::vector<std::pair<int, unsigned long long>> g_uploaded;
 
 const HostModel* host_model(int model) {
   std::lock_guard<std::mutex> lk(g_model_mu);
@@ -244,15 +246,23 @@ int ensure_uploaded(int dev) {
   const HostModel* m1 = host_model(1);
   if (!m0 || !m1) return fail(LBM_EINVAL, "model table solve failed");
   std::lock_guard<std::mutex> lk(g_model_mu);
-  for (int d : g_uploaded)
-    if (d == dev) return LBM_OK;
+  const unsigned long long id = lbm::current_context_id();
+  for (const auto& u : g_uploaded)
+    if (u.first == dev && u.second == id && id != 0) return LBM_OK;
   ModelConst both[2] = {m0->mc, m1->mc};
   const StorageOps* all[4] = {&kOpsFP64, &kOpsFP32, &kOpsFP16, &kOpsBF16};
   for (auto* o : all) {
     cudaError_t e = o->upload(both);
     if (e != cudaSuccess) return cuda_fail(e, "constant table upload");
   }
-  g_uploaded.push_back(dev);
+  // the upload made the device's primary context current: record its id
+  const unsigned long long now = lbm::current_context_id();
+  g_uploaded.erase(std::remove_if(g_uploaded.begin(), g_uploaded.end(),
+                                  [dev](const std::pair<int, unsigned long long>& u) {
+                                    return u.first == dev;
+                                  }),
+                   g_uploaded.end());
+  g_uploaded.push_back({dev, now});
   return LBM_OK;
 }
 
@@ -449,6 +459,33 @@ int do_steps(lbm_ctx* c, int64_t n) {
 
 // ---------------------------------------------------------------- internal hooks for adjoint.cu
 namespace lbm {
+unsigned long long current_context_id() {
+  // driver entry points looked up through the runtime once (no link to libcuda)
+  using GetCurrentFn = CUresult (*)(CUcontext*);
+  using GetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrentFn get_current = nullptr;
+  static GetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetIdFn>(f);
+    cudaGetLastError();
+  });
+  if (!get_current || !get_id) return 0;
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+  unsigned long long id = 0;
+  if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
 int ctx_fail(int code, const char* msg) { return fail(code, "%s", msg); }
 int ctx_cuda_fail(cudaError_t e, const char* what) { return cuda_fail(e, what); }
 const ModelConst* ctx_model_const(int model) {
@@ -823,9 +860,23 @@ int lbm_load(lbm_ctx* c, const char* path) {
               (long long)h.dims[2]);
   else if (!(h.omega >= 0.0 && h.omega < 2.0) || h.steps < 0)
     rc = fail(LBM_EINVAL, "%s: bad omega or step count", path);
-  std::vector<char> buf;
   const size_t total = state_bytes(c);
-  char* dst = static_cast<char*>(c->state[0].p);
+  if (rc == LBM_OK) {
+    // a file of the wrong length is refused before anything is uploaded
+    const long here = std::ftell(f);
+    long end = -1;
+    if (here >= 0 && std::fseek(f, 0, SEEK_END) == 0) end = std::ftell(f);
+    if (end < 0 || std::fseek(f, here, SEEK_SET) != 0)
+      rc = fail(LBM_EIO, "%s: cannot determine the file size", path);
+    else if ((size_t)(end - here) != total)
+      rc = fail(LBM_EIO, "%s: %ld bytes of state, the context needs %zu (truncated or foreign file)",
+                path, end - here, total);
+  }
+  // The state goes into the spare ping-pong buffer; the context switches to it only
+  // once every piece has arrived, so a failed load leaves the live state untouched.
+  std::vector<char> buf;
+  const int spare = c->cur ^ 1;
+  char* dst = static_cast<char*>(c->state[spare].p);
   for (size_t off = 0; rc == LBM_OK && off < total; off += kFileChunk) {
     const size_t m = std::min(kFileChunk, total - off);
     buf.resize(m);
@@ -839,7 +890,7 @@ int lbm_load(lbm_ctx* c, const char* path) {
   }
   std::fclose(f);
   if (rc != LBM_OK) return rc;
-  c->cur = 0;
+  c->cur = spare;
   c->steps = h.steps;
   c->omega = h.omega;
   c->inited = true;

@@ -82,7 +82,7 @@ _sig = {
     "lbm_release_record": (_i, [_vp]),
     "lbm_synchronize": (_i, [_vp]),
     "lbm_launch_count": (_i64, [_vp]),
-    "lbm_audit_noalloc": (_i, [_i, _i, ctypes.POINTER(_i64), _vp, _vp, _vp]),
+    "lbm_audit_noalloc": (_i, [_i, _i, ctypes.POINTER(_i64), _vp, ctypes.c_size_t, _vp, _vp]),
     "lbm_equation_count": (_i, [_i, _i, ctypes.POINTER(_i64)]),
     "lbm_generate_model": (_i, [_i, _i, _i, _vp, _i, _i, ctypes.POINTER(_i), _vp, _vp,
                                 ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_i)]),
@@ -349,15 +349,21 @@ def lbm_launch_count(ctx):
 
 def lbm_audit_noalloc(model, storage, dims, h, out, stream=None):
     """Audit of a caller-owned device population array into a caller-owned device
-    buffer of 8 doubles, without any device allocation (see include/lbm.h)."""
+    buffer of 8 doubles, without any device allocation (see include/lbm.h).
+
+    h and out are torch tensors; the library itself refuses host memory, another
+    device's memory and an h smaller than the grid's populations (LBM_EINVAL)."""
     import torch
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
     elif hasattr(stream, "cuda_stream"):
         stream = stream.cuda_stream
+    if out.dtype != torch.float64 or out.numel() < 8:
+        raise ValueError("out must be a float64 tensor of at least 8 elements")
     d = (_i64 * 3)(*[int(x) for x in dims])
     _check(_lib.lbm_audit_noalloc(MODELS.get(model, model), STORAGES.get(storage, storage), d,
-                                  _ptr(h)[0], _ptr(out)[0], stream), "lbm_audit_noalloc")
+                                  _ptr(h)[0], _nbytes(h), _ptr(out)[0], stream),
+           "lbm_audit_noalloc")
 
 
 def lbm_strerror(code):

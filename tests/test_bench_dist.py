@@ -54,7 +54,7 @@ def test_bench_cli_and_legs_are_wired():
                           "--grid", "32x8x8"])
     assert (a.steps, a.warmup, a.leg, a.storage, a.grid) == (7, 3, "adjoint", "fp16", "32x8x8")
     for name in ("forms_leg", "adjoint_leg", "large_leg", "moments_leg", "d2q33_leg", "e2e_leg", "cpu_baseline_leg",
-                 "run_reference", "run_ours"):
+                 "l2_assisted_leg", "run_reference", "run_ours"):
         assert callable(getattr(bench, name)), name
     assert len(bench.kernel_source_hash()) == 16
 
@@ -82,4 +82,10 @@ def test_reference_arm_prints_the_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
-    assert d["config"]["workload"] == "d3q95_riemann_128x64x64"
+    # the reference arm prints our arm's config object for the same workload; the
+    # sub-box it actually steps is named outside it
+    from paper_1303_4624_gb300 import workloads as W
+    assert d["config"]["workload"] == "d3q95_sweep_512x256x256"
+    wl = W.Workload("d3q95_sweep_512x256x256", "D3Q95", "fp32", (512, 256, 256), 200, 1.8)
+    assert d["config"] == bench.workload_config(wl, 95)
+    assert d["sample_grid"].startswith("512x") and d["sample_grid"] in cb["sample"]

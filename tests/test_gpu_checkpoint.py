@@ -56,11 +56,24 @@ def test_load_rejects_mismatched_or_damaged_files(lbm, tmp_path):
     with pytest.raises(lbm.LbmError) as ei:
         lbm.lbm_load(a.ctx, bad)
     assert ei.value.code == lbm.LBM_EINVAL
-    short = str(tmp_path / "short.lbm")
-    open(short, "wb").write(raw[:len(raw) // 2])
-    with pytest.raises(lbm.LbmError) as ei:
-        lbm.lbm_load(a.ctx, short)
-    assert ei.value.code == lbm.LBM_EIO
+    # truncated (or over-long) files are refused and the live state stays as it was,
+    # bit for bit, with its step count: a later step continues the original run
+    before = a.raw()
+    ref = lattice(lbm, "fp32")
+    ref.step(3)
+    for name, data in (("short.lbm", raw[:len(raw) // 2]), ("shorter.lbm", raw[:72 + 16]),
+                       ("long.lbm", raw + b"\0" * 64)):
+        p = str(tmp_path / name)
+        open(p, "wb").write(data)
+        with pytest.raises(lbm.LbmError) as ei:
+            lbm.lbm_load(a.ctx, p)
+        assert ei.value.code == lbm.LBM_EIO
+        assert lbm.lbm_steps_done(a.ctx) == 3
+        assert np.array_equal(before.view(np.uint8), a.raw().view(np.uint8))
+    a.step(4)
+    ref.step(4)
+    assert np.array_equal(ref.raw().view(np.uint8), a.raw().view(np.uint8))
+    ref.close()
     with pytest.raises(lbm.LbmError) as ei:
         lbm.lbm_load(a.ctx, str(tmp_path / "missing.lbm"))
     assert ei.value.code == lbm.LBM_EIO
