@@ -55,6 +55,8 @@ def parse_args(argv=None):
     p.add_argument("--grid", default="512x256x256", help="NXxNYxNZ of the D3Q95 workload")
     p.add_argument("--setup", default="sweep", choices=["sweep", "riemann"],
                    help="sweep: omega 1.8, (1, 1) | (0.5, 0.8); riemann: omega 1.6, (1, 1) | (0.6, 0.75)")
+    p.add_argument("--variant", default="auto", choices=["auto", "direct", "tma", "split"],
+                   help="stream-collide kernel of the timed workload (auto: the library's choice)")
     p.add_argument("--no-extras", action="store_true", help="skip the forms / adjoint / cpu legs")
     p.add_argument("--leg", default=None, choices=["forms", "adjoint", "large", "moments", "d2q33",
                                                    "l2_assisted"],
@@ -192,8 +194,13 @@ def time_steps(lbm, lat, steps, warmup, stream):
 GRAPH_STEPS = 32     # steps per CUDA-graph replay in lbm_step (captured before timing)
 
 
-def make_lattice(lbm, wl, fields, storage=None):
+VARIANTS = {"auto": 0, "direct": 1, "tma": 2, "split": 3}
+
+
+def make_lattice(lbm, wl, fields, storage=None, variant="auto"):
     lat = lbm.Lattice(wl.model, wl.dims, wl.omega, storage or wl.storage)
+    if VARIANTS[variant]:
+        lbm.lbm_set_variant(lat.ctx, VARIANTS[variant])
     lbm.lbm_set_graph_steps(lat.ctx, GRAPH_STEPS)
     lat.init(fields.rho, fields.U, fields.theta * lat.info["T0"])
     return lat
@@ -258,7 +265,7 @@ def run_ours(args):
     make = W.d3q95_sweep if args.setup == "sweep" else W.d3q95_riemann
     wl, fields = make(nx, ny, nz, storage=args.storage)
     Q = lbm.lbm_model_info(wl.model)["Q"]
-    lat = make_lattice(lbm, wl, fields)
+    lat = make_lattice(lbm, wl, fields, variant=args.variant)
     audit0 = lat.audit()
     launches0 = lbm.lbm_launch_count(lat.ctx)
 
@@ -306,6 +313,7 @@ def run_ours(args):
         "parallelism": "replicas" if world > 1 else "single GPU",
         "launch": "CUDA graphs of %d steps (programmatic dependent launch between steps), "
                   "remainder launched directly" % GRAPH_STEPS,
+        "kernel_variant": args.variant,
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"
                      if peak_kind == "measured" else "fallback 6.8 TB/s",

@@ -125,16 +125,19 @@ int lbm_set_omega(lbm_ctx* ctx, double omega);
 /*
  * lbm_set_variant - choose the stream-collide kernel (same arithmetic, bitwise
  * identical results):
- *   0 (default) direct;
+ *   0 (default) the measured fastest for the context's form (see lbm_step);
  *   1 direct gather: one thread per cell loads its Q populations from HBM;
- *   2 staged: persistent CTAs stream each 128-cell row segment of all Q shifted
- *     source rows into shared memory with bulk asynchronous copies (mbarrier
- *     pipeline, waits bounded at 2 s; a timeout sets the status that
- *     lbm_synchronize reports as LBM_EDEVICE).  Needs Nx % 8 == 0;
+ *   2 TMA: persistent CTAs of 128 threads; warp 0 streams the Q shifted source row
+ *     segments of each 128-cell chunk into a ring of shared-memory stages with bulk
+ *     asynchronous copies (full / empty mbarrier pipeline), the threads read their
+ *     populations at compile-time offsets, and in the FP16 / BF16 forms the
+ *     results leave through a shared-memory tile and bulk stores.  Every wait is
+ *     bounded (1 s); a timeout sets the status that lbm_synchronize reports as
+ *     LBM_EDEVICE.  Needs Nx % 8 == 0;
  *   3 split: the directions of each cell are divided between two warps that
  *     exchange partial moments through shared memory (half the registers per
  *     thread, twice the resident warps).  FP32 / FP16 / BF16 forms only.
- * Errors: LBM_EINVAL.
+ * Errors: LBM_EINVAL, LBM_ECUDA (set-up of the TMA kernel).
  */
 int lbm_set_variant(lbm_ctx* ctx, int variant);
 
@@ -314,6 +317,20 @@ int lbm_release_record(lbm_ctx* ctx);
 /* lbm_synchronize - wait for all work on the context's stream; LBM_EDEVICE if
  * a kernel of the context reported a timed-out wait. */
 int lbm_synchronize(lbm_ctx* ctx);
+
+/*
+ * lbm_test_stall (test hook of the failure detection; the paper has no
+ * counterpart) - the next TMA stream-collide launch of this context (variant 2
+ * must be selected) skips the copies of chunk `chunk` (128 cells of one x-row,
+ * chunks numbered x-segment fastest, then y, then z) and bounds every wait by
+ * limit_ns nanoseconds (1 us .. 2 s).  The consumers of that chunk wait for
+ * copies that never come, give up after limit_ns, set the device status and
+ * stop; lbm_synchronize then returns LBM_EDEVICE once (and clears the status).
+ * Nothing faults and nothing waits without a bound; the state of that step is
+ * incomplete, so reinitialise it afterwards.  That launch is made directly, not
+ * from a CUDA graph.  Errors: LBM_EINVAL, LBM_ESTATE (TMA variant not selected).
+ */
+int lbm_test_stall(lbm_ctx* ctx, int64_t chunk, int64_t limit_ns);
 
 /* lbm_launch_count - kernels this context has launched so far. */
 int64_t lbm_launch_count(const lbm_ctx* ctx);

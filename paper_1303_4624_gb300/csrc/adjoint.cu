@@ -64,7 +64,7 @@ int advance(Sweep& w, const void* src, int64_t k, void* dst, void* work0, void* 
   for (int64_t j = 0; j < k; ++j) {
     void* out = (j == k - 1) ? dst : (((k - 1 - j) & 1) ? a : b);
     cudaError_t e = w.v.ops->step(w.v.model, cur, out, w.v.g, w.v.omega, w.v.variant, w.v.status,
-                                  w.v.stream);
+                                  nullptr, w.v.stream);
     if (e != cudaSuccess) return ctx_cuda_fail(e, "recompute launch");
     *w.v.launches += 1;
     cur = out;
@@ -148,7 +148,7 @@ int lbm_record(lbm_ctx* ctx, int64_t nsteps, int64_t ckpt_every) {
       dst = v.state[pp]->p;
       pp ^= 1;
     }
-    e = v.ops->step(v.model, cur, dst, v.g, v.omega, v.variant, v.status, v.stream);
+    e = v.ops->step(v.model, cur, dst, v.g, v.omega, v.variant, v.status, nullptr, v.stream);
     if (e != cudaSuccess) return ctx_cuda_fail(e, "stream_collide launch");
     *v.launches += 1;
     cur = dst;
@@ -185,7 +185,7 @@ int lbm_record_bounded(lbm_ctx* ctx, int64_t nsteps, int64_t max_states) {
   const void* cur = r.ckpt[0]->p;
   for (int64_t s = 0; s < nsteps; ++s) {
     void* dst = v.state[s & 1]->p;
-    e = v.ops->step(v.model, cur, dst, v.g, v.omega, v.variant, v.status, v.stream);
+    e = v.ops->step(v.model, cur, dst, v.g, v.omega, v.variant, v.status, nullptr, v.stream);
     if (e != cudaSuccess) return ctx_cuda_fail(e, "stream_collide launch");
     *v.launches += 1;
     cur = dst;
@@ -274,7 +274,7 @@ int lbm_backward(lbm_ctx* ctx, const double* dL_drhoN, double* dL_drho0, double*
       states[j] = r.seg[j - 1]->p;
       if (kept) continue;
       cudaError_t e = v.ops->step(v.model, states[j - 1], states[j], v.g, v.omega, v.variant,
-                                   v.status, v.stream);
+                                   v.status, nullptr, v.stream);
       if (e != cudaSuccess) return ctx_cuda_fail(e, "replay launch");
       *v.launches += 1;
     }

@@ -30,6 +30,13 @@ struct Grid {
   long long ncell;
 };
 
+// Failure-detection test of the TMA kernel's bounded waits: the producer skips the
+// copies of chunk stall_chunk, so its consumers' wait runs out after limit_ns.
+struct StepTest {
+  long long stall_chunk;
+  unsigned long long limit_ns;
+};
+
 // Launchers of one storage form (one translation unit each).  All enqueue on
 // `st` and return the launch status.
 struct StorageOps {
@@ -37,11 +44,15 @@ struct StorageOps {
   cudaError_t (*upload)(const ModelConst* mc2);
   cudaError_t (*init)(int model, const double* rho, const double* U, const double* T, void* dst,
                       const Grid& g, cudaStream_t st);
-  // One stream-collide step.  variant: kVariantDirect or kVariantStaged (the caller
-  // checks kVariantStaged is applicable: Nx % 8 == 0).  status: device int set to 1
-  // if a staged launch gave up waiting for its copies.
+  // One stream-collide step.  variant: kVariantDirect, kVariantTma or kVariantSplit
+  // (the caller checks kVariantTma is applicable: Nx % 8 == 0).  status: device int
+  // set to 1 if a TMA launch gave up waiting for its copies.  test: NULL, or the
+  // failure-detection test setting of a TMA launch (see StepTest).
   cudaError_t (*step)(int model, const void* src, void* dst, const Grid& g, double omega,
-                      int variant, int* status, cudaStream_t st);
+                      int variant, int* status, const StepTest* test, cudaStream_t st);
+  // One-time per-device launch set-up of the TMA kernels (shared-memory opt-in and
+  // occupancy), done before any stream capture.
+  cudaError_t (*prepare_tma)(int model);
   cudaError_t (*moments)(int model, const void* src, const Grid& g, double* rho, double* U,
                          double* T, double* partials, cudaStream_t st);
   cudaError_t (*get_f)(int model, const void* src, double* f, const Grid& g, cudaStream_t st);
@@ -74,13 +85,13 @@ cudaError_t launch_sum_reduce(const double* partials, long long n, double* out, 
 extern const StorageOps kOpsFP64, kOpsFP32, kOpsFP16, kOpsBF16;
 
 constexpr int kVariantDirect = 1;
-constexpr int kVariantStaged = 2;
+constexpr int kVariantTma = 2;
 constexpr int kVariantSplit = 3;
 // Or-ed into the variant of a direct-kernel step: walk the blocks in reverse order.
 // Alternate steps walk opposite ways, so each step starts on the cells its
 // predecessor wrote last, which are still in L2.
 constexpr int kStepReverse = 0x100;
-inline bool staged_applicable(const Grid& g) { return g.nx % 8 == 0; }
+inline bool tma_applicable(const Grid& g) { return g.nx % 8 == 0; }
 
 constexpr int kAuditSlots = 8;
 constexpr int kMomentThreads = 256;

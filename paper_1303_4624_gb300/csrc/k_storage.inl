@@ -4,6 +4,7 @@
 #include <mutex>
 
 #include "kernels.cuh"
+#include "stream_collide_tma.cuh"
 #include "adjoint_kernels.cuh"
 
 namespace lbm {
@@ -24,72 +25,108 @@ cudaError_t init_m(const double* rho, const double* U, const double* T, void* ds
   return cudaGetLastError();
 }
 
-// Staged-kernel configuration per storage type: pipeline depth and CTAs per SM
-// (shared memory per CTA = STAGES * Q * (128 + 16) * sizeof(S)).
-template <class T>
-struct StagedCfg {
-  static constexpr int kStages = 2, kMinBlocks = 2;
+// TMA-kernel configuration per model and storage type: pipeline depth, resident CTAs
+// per SM the registers are capped for, and whether the results go out through a
+// shared-memory tile and bulk stores (16-bit forms) or straight from the threads.
+// Shared memory per CTA = STAGES x (stage of Q shifted row segments) + output tile:
+// D3Q95 FP16 2 x 25,440 + 24,320 B (3 CTAs per SM); D2Q33 FP16 3 x 8,864 + 8,448 B.
+template <int M, class T>
+struct TmaCfg {
+  static constexpr int kStages = 2;
+  static constexpr int kMinBlocks = (M == 1) ? 2 : 3;     // FP32
+  static constexpr bool kOutSmem = false;
 };
-template <>
-struct StagedCfg<double> {
-  static constexpr int kStages = 2, kMinBlocks = 1;
+template <int M>
+struct TmaCfg<M, double> {
+  static constexpr int kStages = 2;
+  static constexpr int kMinBlocks = (M == 1) ? 1 : 2;
+  static constexpr bool kOutSmem = false;
 };
-template <>
-struct StagedCfg<__half> {
-  static constexpr int kStages = 2, kMinBlocks = 4;
+template <int M>
+struct TmaCfg<M, __half> {
+  static constexpr int kStages = (M == 1) ? 2 : 3;
+  static constexpr int kMinBlocks = (M == 1) ? 3 : 6;
+  static constexpr bool kOutSmem = true;
 };
-template <>
-struct StagedCfg<__nv_bfloat16> {
-  static constexpr int kStages = 2, kMinBlocks = 4;
+template <int M>
+struct TmaCfg<M, __nv_bfloat16> : TmaCfg<M, __half> {};
+
+template <int M>
+struct TmaKernel {
+  using C = TmaCfg<M, S>;
+  using Smem = TmaSmem<M, S, C::kStages, C::kOutSmem>;
+  static constexpr auto kern = k_stream_collide_tma<M, S, C::kStages, C::kMinBlocks, C::kOutSmem>;
 };
 
 struct LaunchCache {
   int dev = -1;
   int grid = 0;
 };
+std::mutex g_tma_mu;
+LaunchCache g_tma_cache[2][16];
 
+// Shared-memory opt-in and the persistent grid (resident CTAs per SM x SMs), once
+// per device and model.
 template <int M>
-cudaError_t step_staged_m(const void* src, void* dst, const Grid& g, double omega, int* status,
-                          cudaStream_t st) {
-  constexpr int STAGES = StagedCfg<S>::kStages, MINB = StagedCfg<S>::kMinBlocks;
-  using Lay = StageLayout<S, STAGES, Model<M>::Q>;
-  auto kern = k_stream_collide_staged<M, S, STAGES, MINB>;
-  static std::mutex mu;
-  static LaunchCache cache[16];
+cudaError_t prepare_tma_m(int* grid_out) {
+  using K = TmaKernel<M>;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  int per_sm_grid;
-  {
-    std::lock_guard<std::mutex> lk(mu);
-    LaunchCache& lc = cache[dev & 15];
-    if (lc.dev != dev) {
-      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::kBytes);
-      if (e != cudaSuccess) return e;
-      int per_sm = 0, sms = 0;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kStageW, Lay::kBytes);
-      if (e != cudaSuccess) return e;
-      e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      if (e != cudaSuccess) return e;
-      if (per_sm < 1) return cudaErrorInvalidConfiguration;
-      lc.grid = per_sm * sms;
-      lc.dev = dev;
-    }
-    per_sm_grid = lc.grid;
+  std::lock_guard<std::mutex> lk(g_tma_mu);
+  LaunchCache& lc = g_tma_cache[M][dev & 15];
+  if (lc.dev != dev) {
+    e = cudaFuncSetAttribute(K::kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::Smem::kBytes);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, K::kern, kTmaW, K::Smem::kBytes);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    lc.grid = per_sm * sms;
+    lc.dev = dev;
   }
-  const long long nchunks = (long long)((g.nx + kStageW - 1) / kStageW) * g.ny * g.nz;
-  const int grid = (int)(nchunks < per_sm_grid ? nchunks : per_sm_grid);
-  kern<<<grid, kStageW, Lay::kBytes, st>>>(static_cast<const S*>(src), static_cast<S*>(dst), g, omega,
-                                         (int)nchunks, status);
-  return cudaGetLastError();
+  if (grid_out) *grid_out = lc.grid;
+  return cudaSuccess;
+}
+
+cudaError_t prepare_tma(int m) {
+  return m == 0 ? prepare_tma_m<0>(nullptr) : prepare_tma_m<1>(nullptr);
+}
+
+template <int M>
+cudaError_t step_tma_m(const void* src, void* dst, const Grid& g, double omega, int* status,
+                       const StepTest* test, cudaStream_t st) {
+  using K = TmaKernel<M>;
+  int cap = 0;
+  cudaError_t e = prepare_tma_m<M>(&cap);
+  if (e != cudaSuccess) return e;
+  const long long nchunks = (long long)((g.nx + kTmaW - 1) / kTmaW) * g.ny * g.nz;
+  const int grid = (int)(nchunks < cap ? nchunks : cap);
+  TmaTest t;
+  t.stall_chunk = test ? test->stall_chunk : -1;
+  t.limit_ns = test ? test->limit_ns : 1000000000ull;   // 1 s: far beyond any copy's latency
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kTmaW);
+  cfg.dynamicSmemBytes = K::Smem::kBytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, K::kern, static_cast<const S*>(src), static_cast<S*>(dst), g,
+                            omega, (int)nchunks, status, t);
 }
 
 template <int M>
 cudaError_t step_m(const void* src, void* dst, const Grid& g, double omega, int variant, int* status,
-                   cudaStream_t st) {
+                   const StepTest* test, cudaStream_t st) {
   const int rev = (variant & kStepReverse) ? 1 : 0;
   variant &= ~kStepReverse;
-  if (variant == kVariantStaged) return step_staged_m<M>(src, dst, g, omega, status, st);
+  if (variant == kVariantTma) return step_tma_m<M>(src, dst, g, omega, status, test, st);
   if constexpr (!std::is_same<S, double>::value) {
     if (variant == kVariantSplit) {
       constexpr int cells = kSplitThreads / 2;
@@ -226,9 +263,9 @@ cudaError_t init(int m, const double* rho, const double* U, const double* T, voi
   return m == 0 ? init_m<0>(rho, U, T, dst, g, st) : init_m<1>(rho, U, T, dst, g, st);
 }
 cudaError_t step(int m, const void* src, void* dst, const Grid& g, double omega, int variant,
-                 int* status, cudaStream_t st) {
-  return m == 0 ? step_m<0>(src, dst, g, omega, variant, status, st)
-                : step_m<1>(src, dst, g, omega, variant, status, st);
+                 int* status, const StepTest* test, cudaStream_t st) {
+  return m == 0 ? step_m<0>(src, dst, g, omega, variant, status, test, st)
+                : step_m<1>(src, dst, g, omega, variant, status, test, st);
 }
 cudaError_t moments(int m, const void* src, const Grid& g, double* rho, double* U, double* T,
                     double* partials, cudaStream_t st) {
@@ -244,7 +281,7 @@ cudaError_t set_f(int m, const double* f, void* dst, const Grid& g, cudaStream_t
 
 }  // namespace
 
-const StorageOps LBM_OPS = {(int)sizeof(S), upload,       init,      step,
+const StorageOps LBM_OPS = {(int)sizeof(S), upload,       init,      step,         prepare_tma,
                             moments,        get_f,        set_f,     fix_ends,
                             (int)sizeof(L), adjoint_step, grad_init};
 

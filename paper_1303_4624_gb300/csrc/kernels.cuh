@@ -434,15 +434,14 @@ struct FormOpts {
   static constexpr bool kExact = sizeof(S) >= 4;
 };
 
-template <int M, class S, class Load, class Store>
-__device__ __forceinline__ void cell_update(Load&& ld, double omega, Store&& st) {
+// a3 - a6 of one cell from its gathered, decoded populations h[Q].
+template <int M, class S, class Store>
+__device__ __forceinline__ void cell_collide(const typename Codec<S>::R (&h)[Model<M>::Q],
+                                             double omega, Store&& st) {
   using Mo = Model<M>;
   using Rt = typename Codec<S>::R;
-  constexpr int Q = Mo::Q, NP = Mo::NP, NH = NP / 2;
+  constexpr int NP = Mo::NP, NH = NP / 2;
   constexpr bool SH = FormOpts<S>::kShell, EX = FormOpts<S>::kExact;
-  // a1 + a2
-  Rt h[Q];
-  sfor<0, Q>([&](auto I) { h[decltype(I)::value] = ld(I); });
   auto hv = [&](auto I) { return h[decltype(I)::value]; };
   // a3, a4
   const HalfMoments<Rt> A = half_moments<M, Rt, 0, NH, true, SH>(hv);
@@ -451,6 +450,16 @@ __device__ __forceinline__ void cell_update(Load&& ld, double omega, Store&& st)
   // a5, a6
   half_collide<M, Rt, 0, NH, true, EX>(c, omega, hv, st);
   half_collide<M, Rt, NH, NP, false, EX>(c, omega, hv, st);
+}
+
+// One cell update: a1 + a2 through the load functor (all Q loads issued before any
+// use), then cell_collide.
+template <int M, class S, class Load, class Store>
+__device__ __forceinline__ void cell_update(Load&& ld, double omega, Store&& st) {
+  using Rt = typename Codec<S>::R;
+  Rt h[Model<M>::Q];
+  sfor<0, Model<M>::Q>([&](auto I) { h[decltype(I)::value] = ld(I); });
+  cell_collide<M, S>(h, omega, st);
 }
 
 // Periodic index for -n <= v < 2n (one correction each way).
@@ -618,182 +627,6 @@ __global__ void __launch_bounds__(kSplitThreads, LBM_SPLIT_MINB)
     half_update<M, S, 0>(ld, omega, st, xch, pair, lane);
   else
     half_update<M, S, 1>(ld, omega, st, xch, pair, lane);
-}
-
-// ----------------------------------------------------------------- staged (TMA bulk) kernel
-// Persistent CTAs of kStageW threads walk "chunks" (kStageW consecutive cells of one
-// x-row).  For each chunk, warp 0 streams the kStageW + 2 kStagePad elements of every
-// direction's source row (the shifted plane of that direction: row (y - e_y, z - e_z),
-// x from x0 - kStagePad, periodic) from HBM into shared memory with cp.async.bulk,
-// completing on the stage's mbarrier; STAGES chunks are in flight.  Each thread then
-// reads its Q populations at compile-time offsets (no address arithmetic), updates the
-// cell, and stores the Q results.  Needs Nx a multiple of 8 (16-byte copies).
-constexpr int kStageW = 128;
-constexpr int kStagePad = 8;
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// Wait for an mbarrier phase, giving up after limit_ns of wall time.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  while (true) {
-    for (int k = 0; k < 64; ++k)
-      if (mbar_try_wait(bar, parity)) return true;
-    if (global_ns() - t0 > limit_ns) return false;
-  }
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
-                                         uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          dst),
-      "l"(src), "r"(bytes), "r"(bar)
-      : "memory");
-}
-
-template <class S>
-__device__ __forceinline__ typename Codec<S>::R lds(const S* p) {
-  if constexpr (std::is_same<S, __half>::value)
-    return __half2float(*p);
-  else if constexpr (std::is_same<S, __nv_bfloat16>::value)
-    return __bfloat162float(*p);
-  else
-    return *p;
-}
-
-template <class S, int STAGES, int Q>
-struct StageLayout {
-  static constexpr int kRow = kStageW + 2 * kStagePad;      // elements per staged row
-  static constexpr int kStageElems = Q * kRow;
-  static constexpr size_t kDataBytes = (size_t)STAGES * kStageElems * sizeof(S);
-  static constexpr size_t kBytes = kDataBytes + STAGES * sizeof(unsigned long long);
-};
-
-template <int M, class S, int STAGES, int MINB>
-__global__ void __launch_bounds__(kStageW, MINB)
-    k_stream_collide_staged(const S* __restrict__ src, S* __restrict__ dst, Grid g, double omega,
-                            int nchunks, int* __restrict__ status) {
-  using Mo = Model<M>;
-  constexpr int Q = Mo::Q;
-  using L = StageLayout<S, STAGES, Q>;
-  constexpr uint64_t kLimitNs = 2000000000ull;    // 2 s: far beyond any real copy latency
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  S* stage_mem = reinterpret_cast<S*>(smem_raw);
-  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem_raw + L::kDataBytes);
-  __shared__ int sdir[Q][3];
-
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int i = tid; i < Q; i += blockDim.x) {
-    sdir[i][0] = c_mc[M].e[i][0];
-    sdir[i][1] = c_mc[M].e[i][1];
-    sdir[i][2] = c_mc[M].e[i][2];
-  }
-  if (tid == 0) {
-    for (int s = 0; s < STAGES; ++s) mbar_init(smem_addr(&bars[s]), 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-
-  const int nxc = (g.nx + kStageW - 1) / kStageW;
-  auto issue = [&](int c, int stage) {   // executed by all lanes of warp 0
-    const int xc = c % nxc, row = c / nxc;
-    const int y = row % g.ny, z = row / g.ny;
-    const int x0 = xc * kStageW;
-    const int wc = min(kStageW, g.nx - x0);
-    const uint32_t bar = smem_addr(&bars[stage]);
-    if (lane == 0) mbar_expect_tx(bar, (uint32_t)(Q * (wc + 2 * kStagePad) * sizeof(S)));
-    __syncwarp();
-    for (int i = lane; i < Q; i += 32) {
-      const int ys = wrapi(y - sdir[i][1], g.ny);
-      const int zs = wrapi(z - sdir[i][2], g.nz);
-      const S* rowp = src + (size_t)i * (size_t)g.ncell + ((size_t)zs * g.ny + ys) * g.nx;
-      const uint32_t d0 = smem_addr(stage_mem + (size_t)stage * L::kStageElems + (size_t)i * L::kRow);
-      int xlo = x0 - kStagePad;
-      const int xhi = x0 + wc + kStagePad;
-      int j = 0;
-      if (xlo < 0) {
-        bulk_g2s(d0, rowp + (g.nx + xlo), (uint32_t)(-xlo * sizeof(S)), bar);
-        j = -xlo;
-        xlo = 0;
-      }
-      const int mhi = min(xhi, g.nx);
-      bulk_g2s(d0 + j * sizeof(S), rowp + xlo, (uint32_t)((mhi - xlo) * sizeof(S)), bar);
-      j += mhi - xlo;
-      if (xhi > g.nx) bulk_g2s(d0 + j * sizeof(S), rowp, (uint32_t)((xhi - g.nx) * sizeof(S)), bar);
-    }
-  };
-
-  const int G = gridDim.x;
-  if (warp == 0)
-    for (int s = 0; s < STAGES - 1; ++s) {
-      const int c = blockIdx.x + s * G;
-      if (c < nchunks) issue(c, s);
-    }
-  int k = 0;
-  bool failed = false;
-  for (int c = blockIdx.x; c < nchunks; c += G, ++k) {
-    const int stage = k % STAGES;
-    if (warp == 0) {
-      const int cn = c + (STAGES - 1) * G;
-      if (cn < nchunks) issue(cn, (k + STAGES - 1) % STAGES);
-    }
-    const bool ok = mbar_wait_bounded(smem_addr(&bars[stage]), (uint32_t)((k / STAGES) & 1), kLimitNs);
-    if (__syncthreads_or(!ok)) {
-      failed = true;
-      break;
-    }
-    const int xc = c % nxc, row = c / nxc;
-    const int x0 = xc * kStageW;
-    if (tid < min(kStageW, g.nx - x0)) {
-      const S* sp = stage_mem + (size_t)stage * L::kStageElems + kStagePad + tid;
-      const size_t self = (size_t)row * g.nx + x0 + tid;
-      cell_update<M, S>(
-          [&](auto I) {
-            constexpr int i = decltype(I)::value;
-            constexpr int off = i * L::kRow - Mo::vs.e[i][0];
-            return lds<S>(sp + off);
-          },
-          omega,
-          [&](auto I, typename Codec<S>::R v) {
-            Codec<S>::st(dst + (size_t)decltype(I)::value * (size_t)g.ncell + self, v);
-          });
-    }
-    __syncthreads();   // the stage is consumed: it may be refilled
-  }
-  if (failed && tid == 0) {
-    atomicExch(status, 1);
-    // drain the copies this CTA still has in flight before its shared memory goes away
-    for (int j = 1; j < STAGES; ++j) {
-      const int kk = k + j;
-      const int cc = blockIdx.x + kk * G;
-      if (cc < nchunks) mbar_wait_bounded(smem_addr(&bars[kk % STAGES]), (uint32_t)((kk / STAGES) & 1), kLimitNs);
-    }
-  }
 }
 
 // ----------------------------------------------------------------- equilibrium init (FP64)

@@ -354,7 +354,9 @@ struct lbm_ctx {
   DevBuf partials;    // audit block partials
   DevBuf audit_out;   // 8 doubles
   DevBuf status;      // device int: 1 after a kernel gave up on a bounded wait
-  int variant = 0;    // 0 auto, kVariantDirect, kVariantStaged
+  int variant = 0;    // 0 auto, kVariantDirect, kVariantTma, kVariantSplit
+  StepTest test{-1, 0};  // lbm_test_stall: applies to the next TMA launch only
+  bool test_pending = false;
   int fix_axis = 0, fix_width = 0;   // fixed-state end planes (width 0: none)
   DevBuf fix_tmpl;    // [Q][2] populations of the two end states
   bool inited = false;
@@ -395,8 +397,13 @@ cudaError_t enqueue_steps(lbm_ctx* c, int64_t n, int variant, int* cur, cudaStre
     // negligible and the descending walk measured ~1 % slower.
     const bool alt = state_bytes(c) <= ((size_t)256 << 20);
     const int v = variant | ((alt && variant == kVariantDirect && *cur == 1) ? kStepReverse : 0);
+    const StepTest* t = nullptr;
+    if (c->test_pending && variant == kVariantTma) {
+      t = &c->test;
+      c->test_pending = false;
+    }
     cudaError_t e = c->ops->step(c->model, c->state[*cur].p, c->state[*cur ^ 1].p, c->g, c->omega,
-                                 v, static_cast<int*>(c->status.p), st);
+                                 v, static_cast<int*>(c->status.p), t, st);
     if (e != cudaSuccess) return e;
     *cur ^= 1;
     if (c->fix_width > 0) {
@@ -411,6 +418,11 @@ cudaError_t enqueue_steps(lbm_ctx* c, int64_t n, int variant, int* cur, cudaStre
 // Capture kGraphSteps steps starting from buffer `parity`.  False (and graphs off for
 // this context) if capture or instantiation fails; the caller then launches directly.
 bool capture_steps(lbm_ctx* c, int parity, int variant) {
+  if (variant == kVariantTma && c->ops->prepare_tma(c->model) != cudaSuccess) {
+    cudaGetLastError();
+    c->graph_steps = 0;
+    return false;
+  }
   if (!c->cap_stream &&
       cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
@@ -440,7 +452,8 @@ int do_steps(lbm_ctx* c, int64_t n) {
   const int variant = pick_variant(c);
   const int64_t per_step = c->fix_width > 0 ? 2 : 1;
   int64_t done = 0;
-  if (c->graph_steps > 0 && variant == kVariantDirect && n >= 2 * c->graph_steps &&
+  if (c->graph_steps > 0 && (variant == kVariantDirect || variant == kVariantTma) &&
+      !c->test_pending && n >= 2 * c->graph_steps &&
       (c->graph.exec[c->cur] || capture_steps(c, c->cur, variant))) {
     for (; n - done >= c->graph_steps; done += c->graph_steps) {
       cudaError_t e = cudaGraphLaunch(c->graph.exec[c->cur], c->stream);
@@ -648,7 +661,7 @@ int lbm_set_graph_steps(lbm_ctx* c, int steps) {
   c->graph_steps = steps;
   // capture both starting buffers now, so that no later lbm_step pays for it
   const int variant = pick_variant(c);
-  if (steps > 0 && variant == kVariantDirect)
+  if (steps > 0 && (variant == kVariantDirect || variant == kVariantTma))
     for (int parity = 0; parity < 2; ++parity)
       if (!capture_steps(c, parity, variant))
         return fail(LBM_ECUDA, "graph capture of the step failed; direct launches stay in use");
@@ -657,13 +670,18 @@ int lbm_set_graph_steps(lbm_ctx* c, int steps) {
 
 int lbm_set_variant(lbm_ctx* c, int variant) {
   if (!c) return fail(LBM_EINVAL, "ctx is NULL");
-  if (variant != 0 && variant != kVariantDirect && variant != kVariantStaged &&
+  if (variant != 0 && variant != kVariantDirect && variant != kVariantTma &&
       variant != kVariantSplit)
     return fail(LBM_EINVAL, "variant %d", variant);
   if (variant == kVariantSplit && c->storage == LBM_FP64)
     return fail(LBM_EINVAL, "the split kernel is for the FP32-arithmetic forms");
-  if (variant == kVariantStaged && !staged_applicable(c->g))
-    return fail(LBM_EINVAL, "the staged kernel needs Nx %% 8 == 0");
+  if (variant == kVariantTma && !tma_applicable(c->g))
+    return fail(LBM_EINVAL, "the TMA kernel needs Nx %% 8 == 0");
+  if (variant == kVariantTma) {
+    DeviceGuard dg(c->dev);
+    cudaError_t e = c->ops->prepare_tma(c->model);
+    if (e != cudaSuccess) return cuda_fail(e, "TMA kernel set-up");
+  }
   c->variant = variant;
   c->graph.reset();
   return LBM_OK;
@@ -1021,7 +1039,23 @@ int lbm_synchronize(lbm_ctx* c) {
   int flag = 0;
   LBM_CUDA(cudaMemcpyAsync(&flag, c->status.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   LBM_CUDA(cudaStreamSynchronize(c->stream));
-  if (flag) return fail(LBM_EDEVICE, "a staged kernel timed out waiting for its copies");
+  if (flag) {
+    // reported once: the flag is cleared for the launches that follow
+    LBM_CUDA(cudaMemsetAsync(c->status.p, 0, sizeof(int), c->stream));
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    return fail(LBM_EDEVICE, "a TMA stream-collide launch timed out waiting for its copies");
+  }
+  return LBM_OK;
+}
+
+int lbm_test_stall(lbm_ctx* c, int64_t chunk, int64_t limit_ns) {
+  if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+  if (chunk < 0 || limit_ns < 1000 || limit_ns > 2000000000LL)
+    return fail(LBM_EINVAL, "chunk >= 0 and 1 us <= limit_ns <= 2 s are required");
+  if (pick_variant(c) != kVariantTma) return fail(LBM_ESTATE, "the TMA variant is not selected");
+  c->test.stall_chunk = chunk;
+  c->test.limit_ns = (unsigned long long)limit_ns;
+  c->test_pending = true;
   return LBM_OK;
 }
 

@@ -28,7 +28,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ESTATE, LBM_EDEVICE, LBM_EIO = \
     0, -1, -2, -3, -4, -5, -6, -7
-VARIANT_AUTO, VARIANT_DIRECT, VARIANT_STAGED, VARIANT_SPLIT = 0, 1, 2, 3
+VARIANT_AUTO, VARIANT_DIRECT, VARIANT_TMA, VARIANT_SPLIT = 0, 1, 2, 3
 LBM_D2Q33, LBM_D3Q95 = 0, 1
 LBM_FP64, LBM_FP32, LBM_FP16DEV, LBM_BF16DEV = 0, 1, 2, 3
 LBM_HOST, LBM_DEVICE = 0, 1
@@ -47,7 +47,7 @@ SYMBOLS = ("lbm_model_info", "lbm_set_allocator", "lbm_create", "lbm_destroy", "
            "lbm_moments", "lbm_audit",
            "lbm_get_populations", "lbm_set_populations", "lbm_get_raw", "lbm_set_raw",
            "lbm_record", "lbm_record_bounded", "lbm_backward", "lbm_release_record", "lbm_synchronize",
-           "lbm_launch_count", "lbm_audit_noalloc", "lbm_equation_count", "lbm_generate_model",
+           "lbm_launch_count", "lbm_test_stall", "lbm_audit_noalloc", "lbm_equation_count", "lbm_generate_model",
            "lbm_strerror", "lbm_last_error")
 
 _vp, _i, _i64, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
@@ -82,6 +82,7 @@ _sig = {
     "lbm_release_record": (_i, [_vp]),
     "lbm_synchronize": (_i, [_vp]),
     "lbm_launch_count": (_i64, [_vp]),
+    "lbm_test_stall": (_i, [_vp, _i64, _i64]),
     "lbm_audit_noalloc": (_i, [_i, _i, ctypes.POINTER(_i64), _vp, ctypes.c_size_t, _vp, _vp]),
     "lbm_equation_count": (_i, [_i, _i, ctypes.POINTER(_i64)]),
     "lbm_generate_model": (_i, [_i, _i, _i, _vp, _i, _i, ctypes.POINTER(_i), _vp, _vp,
@@ -345,6 +346,11 @@ def lbm_synchronize(ctx):
 
 def lbm_launch_count(ctx):
     return int(_lib.lbm_launch_count(ctx))
+
+
+def lbm_test_stall(ctx, chunk, limit_ns):
+    """Test hook: the next TMA launch skips one chunk's copies; its bounded wait runs out."""
+    _check(_lib.lbm_test_stall(ctx, int(chunk), int(limit_ns)), "lbm_test_stall")
 
 
 def lbm_audit_noalloc(model, storage, dims, h, out, stream=None):

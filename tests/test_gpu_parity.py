@@ -276,21 +276,27 @@ def test_d3q95_fp64_full_relaxation_and_near_two(lbm, omega):
 
 
 @pytest.mark.parametrize("storage", ["fp64", "fp32"])
-def test_staged_kernel_matches_oracle_with_ragged_chunk(lbm, storage):
-    """136 x 6 x 5: one full 128-cell chunk and a ragged 8-cell chunk per row, halos
-    wrapping at both row ends, y / z smaller than the reach."""
+def test_tma_kernel_matches_oracle_with_ragged_chunk(lbm, storage):
+    """136 x 6 x 5 with the TMA kernel: one full 128-cell chunk and a ragged 8-cell
+    chunk per row, row segments wrapping at both row ends, y / z smaller than the reach."""
     dims = (136, 6, 5)
     fields = W.riemann_planar(3, *dims, 68, (1.0, 1.0), (0.6, 0.75), seed=6)
     steps = 12 if storage == "fp64" else 40
-    mdl, S, lat = run_both(lbm, "D3Q95", storage, fields, 1.6, steps, dims)
+    mdl, S, lat = run_both(lbm, "D3Q95", storage, fields, 1.6, steps, dims, lbm.VARIANT_TMA)
     compare(mdl, S, lat, TOL[storage])
 
 
+# Grids for the bitwise comparison of the kernel variants: ragged chunks, grids below
+# the reach, and grids with many chunks per persistent TMA CTA (several trips round
+# the stage ring, the output tile reused chunk after chunk).
+VARIANT_GRIDS = [("D3Q95", (136, 6, 5)), ("D3Q95", (8, 3, 4)), ("D3Q95", (256, 64, 32)),
+                 ("D2Q33", (264, 5, 1)), ("D2Q33", (16, 2, 1)), ("D2Q33", (2048, 400, 1))]
+
+
 @pytest.mark.parametrize("storage", ["fp64", "fp32", "fp16", "bf16"])
-@pytest.mark.parametrize("model,dims", [("D3Q95", (136, 6, 5)), ("D3Q95", (8, 3, 4)),
-                                        ("D2Q33", (264, 5, 1)), ("D2Q33", (16, 2, 1))])
+@pytest.mark.parametrize("model,dims", VARIANT_GRIDS)
 def test_kernel_variants_agree_bitwise(lbm, model, dims, storage):
-    """Direct, staged and split (FP32-arithmetic forms) kernels compute the same
+    """Direct, TMA and split (FP32-arithmetic forms) kernels compute the same
     arithmetic in the same order: their states agree bit for bit."""
     mdl = get_model(model)
     rng = np.random.default_rng(7)
@@ -299,7 +305,7 @@ def test_kernel_variants_agree_bitwise(lbm, model, dims, storage):
     U = 0.05 * rng.uniform(-1, 1, (mdl.D,) + shape)
     theta = 1.0 + 0.1 * rng.uniform(-1, 1, shape)
     out = []
-    variants = [lbm.VARIANT_DIRECT, lbm.VARIANT_STAGED]
+    variants = [lbm.VARIANT_DIRECT, lbm.VARIANT_TMA]
     if storage != "fp64":
         variants.append(lbm.VARIANT_SPLIT)
     for variant in variants:
@@ -309,12 +315,50 @@ def test_kernel_variants_agree_bitwise(lbm, model, dims, storage):
         lat.step(9)
         lbm.lbm_synchronize(lat.ctx)
         out.append(lat.raw())
+        lat.close()
     for o in out[1:]:
         assert np.array_equal(out[0].view(np.uint8), o.view(np.uint8))
 
 
-def test_staged_variant_needs_nx_multiple_of_8(lbm):
+def test_tma_variant_needs_nx_multiple_of_8(lbm):
     lat = lbm.Lattice("D3Q95", (12, 4, 4), 1.0, "fp32")
     with pytest.raises(lbm.LbmError) as ei:
-        lbm.lbm_set_variant(lat.ctx, lbm.VARIANT_STAGED)
+        lbm.lbm_set_variant(lat.ctx, lbm.VARIANT_TMA)
     assert ei.value.code == lbm.LBM_EINVAL
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_test_stall(lat.ctx, 0, 10 ** 6)         # the hook needs the TMA variant
+    assert ei.value.code == lbm.LBM_ESTATE
+    lat.close()
+
+
+@pytest.mark.parametrize("storage", ["fp16", "fp32"])
+def test_tma_bounded_wait_runs_out_and_reports(lbm, storage):
+    """Failure detection of the TMA kernel without a fault: the test hook makes the
+    producer skip one chunk's copies, so that chunk's consumers wait for data that
+    never comes; their wait gives up after 20 ms, the CTA stops (after waiting for
+    its other copies in flight), and lbm_synchronize reports LBM_EDEVICE once.  The
+    context stays usable: a fresh run on it matches the direct kernel bit for bit.
+    FP16 covers the path with the shared-memory output tile, FP32 the direct stores."""
+    dims = (256, 64, 32)
+    fields = W.riemann_planar(3, *dims, 128, (1.0, 1.0), (0.6, 0.75), seed=9)
+    lat = lbm.Lattice("D3Q95", dims, 1.6, storage)
+    lbm.lbm_set_graph_steps(lat.ctx, 0)
+    lbm.lbm_set_variant(lat.ctx, lbm.VARIANT_TMA)
+    lat.init(fields.rho, fields.U, fields.theta * lat.info["T0"])
+    lbm.lbm_test_stall(lat.ctx, 777, 20 * 10 ** 6)
+    lat.step(1)
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_synchronize(lat.ctx)
+    assert ei.value.code == lbm.LBM_EDEVICE
+    lbm.lbm_synchronize(lat.ctx)                       # reported once, then cleared
+    lat.init(fields.rho, fields.U, fields.theta * lat.info["T0"])
+    lat.step(5)
+    lbm.lbm_synchronize(lat.ctx)
+    got = lat.raw()
+    lat.close()
+    ref = lbm.Lattice("D3Q95", dims, 1.6, storage)
+    lbm.lbm_set_variant(ref.ctx, lbm.VARIANT_DIRECT)
+    ref.init(fields.rho, fields.U, fields.theta * ref.info["T0"])
+    ref.step(5)
+    assert np.array_equal(got.view(np.uint8), ref.raw().view(np.uint8))
+    ref.close()
