@@ -55,7 +55,7 @@ def parse_args(argv=None):
     p.add_argument("--grid", default="512x256x256", help="NXxNYxNZ of the D3Q95 workload")
     p.add_argument("--setup", default="sweep", choices=["sweep", "riemann"],
                    help="sweep: omega 1.8, (1, 1) | (0.5, 0.8); riemann: omega 1.6, (1, 1) | (0.6, 0.75)")
-    p.add_argument("--variant", default="auto", choices=["auto", "direct", "tma", "split"],
+    p.add_argument("--variant", default="auto", choices=["auto", "direct", "tma", "split", "pair"],
                    help="stream-collide kernel of the timed workload (auto: the library's choice)")
     p.add_argument("--no-extras", action="store_true", help="skip the forms / adjoint / cpu legs")
     p.add_argument("--leg", default=None, choices=["forms", "adjoint", "large", "moments", "d2q33",
@@ -194,7 +194,7 @@ def time_steps(lbm, lat, steps, warmup, stream):
 GRAPH_STEPS = 32     # steps per CUDA-graph replay in lbm_step (captured before timing)
 
 
-VARIANTS = {"auto": 0, "direct": 1, "tma": 2, "split": 3}
+VARIANTS = {"auto": 0, "direct": 1, "tma": 2, "split": 3, "pair": 4}
 
 
 def make_lattice(lbm, wl, fields, storage=None, variant="auto"):

@@ -44,8 +44,9 @@ struct StorageOps {
   cudaError_t (*upload)(const ModelConst* mc2);
   cudaError_t (*init)(int model, const double* rho, const double* U, const double* T, void* dst,
                       const Grid& g, cudaStream_t st);
-  // One stream-collide step.  variant: kVariantDirect, kVariantTma or kVariantSplit
-  // (the caller checks kVariantTma is applicable: Nx % 8 == 0).  status: device int
+  // One stream-collide step.  variant: kVariantDirect, kVariantTma, kVariantSplit or
+  // kVariantPair, or-ed with kStepReverse for the direct and pair kernels (the caller
+  // checks applicability: Nx % 8 == 0 for TMA, Nx even and 16-bit storage for pair).  status: device int
   // set to 1 if a TMA launch gave up waiting for its copies.  test: NULL, or the
   // failure-detection test setting of a TMA launch (see StepTest).
   cudaError_t (*step)(int model, const void* src, void* dst, const Grid& g, double omega,
@@ -87,11 +88,13 @@ extern const StorageOps kOpsFP64, kOpsFP32, kOpsFP16, kOpsBF16;
 constexpr int kVariantDirect = 1;
 constexpr int kVariantTma = 2;
 constexpr int kVariantSplit = 3;
+constexpr int kVariantPair = 4;   // two cells per thread, paired FP32 (FP16 / BF16 forms)
 // Or-ed into the variant of a direct-kernel step: walk the blocks in reverse order.
 // Alternate steps walk opposite ways, so each step starts on the cells its
 // predecessor wrote last, which are still in L2.
 constexpr int kStepReverse = 0x100;
 inline bool tma_applicable(const Grid& g) { return g.nx % 8 == 0; }
+inline bool pair_applicable(const Grid& g) { return g.nx % 2 == 0; }
 
 constexpr int kAuditSlots = 8;
 constexpr int kMomentThreads = 256;

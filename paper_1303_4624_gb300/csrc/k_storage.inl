@@ -5,6 +5,7 @@
 
 #include "kernels.cuh"
 #include "stream_collide_tma.cuh"
+#include "stream_collide_pair.cuh"
 #include "adjoint_kernels.cuh"
 
 namespace lbm {
@@ -127,6 +128,25 @@ cudaError_t step_m(const void* src, void* dst, const Grid& g, double omega, int 
   const int rev = (variant & kStepReverse) ? 1 : 0;
   variant &= ~kStepReverse;
   if (variant == kVariantTma) return step_tma_m<M>(src, dst, g, omega, status, test, st);
+  if constexpr (sizeof(S) == 2) {
+    if (variant == kVariantPair) {
+      const int cells = 2 * kPairThreads;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)((g.nx + cells - 1) / cells), (unsigned)g.ny, (unsigned)g.nz);
+      cfg.blockDim = dim3(kPairThreads);
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      if (rev)
+        return cudaLaunchKernelEx(&cfg, k_stream_collide_pair<M, S, true>, static_cast<const S*>(src),
+                                  static_cast<S*>(dst), g, omega);
+      return cudaLaunchKernelEx(&cfg, k_stream_collide_pair<M, S, false>, static_cast<const S*>(src),
+                                static_cast<S*>(dst), g, omega);
+    }
+  }
   if constexpr (!std::is_same<S, double>::value) {
     if (variant == kVariantSplit) {
       constexpr int cells = kSplitThreads / 2;

@@ -97,17 +97,36 @@ __device__ __forceinline__ int wrapi(int v, int n) {
   return v;
 }
 
+// Arithmetic types: double (FP64 form), float (one cell per thread) and float2 (two
+// cells per thread: lane .x is one cell, lane .y the next; every operation below
+// acts on each lane exactly as the float operation does, through the paired FP32
+// instructions of sm_100+, so both lanes round as the scalar code would).
+template <class R>
+struct IsPair : std::false_type {};
+template <>
+struct IsPair<float2> : std::true_type {};
+
+// A constant in the arithmetic type.
+template <class R>
+__device__ __forceinline__ R cst(double v) {
+  if constexpr (IsPair<R>::value) return make_float2((float)v, (float)v); else return (R)v;
+}
+template <class R>
+__device__ __forceinline__ R splat(float v) {
+  if constexpr (IsPair<R>::value) return make_float2(v, v); else return (R)v;
+}
+
 template <class R>
 __device__ __forceinline__ R gW(const ModelConst& mc, int g) {
-  if constexpr (std::is_same<R, double>::value) return mc.W[g]; else return mc.Wf[g];
+  if constexpr (std::is_same<R, double>::value) return mc.W[g]; else return splat<R>(mc.Wf[g]);
 }
 template <class R>
 __device__ __forceinline__ R gA(const ModelConst& mc) {
-  if constexpr (std::is_same<R, double>::value) return mc.a; else return mc.af;
+  if constexpr (std::is_same<R, double>::value) return mc.a; else return splat<R>(mc.af);
 }
 template <class R>
 __device__ __forceinline__ R gX2(const ModelConst& mc, int g) {
-  if constexpr (std::is_same<R, double>::value) return mc.X2[g]; else return mc.X2f[g];
+  if constexpr (std::is_same<R, double>::value) return mc.X2[g]; else return splat<R>(mc.X2f[g]);
 }
 
 // Explicitly rounded arithmetic for the stream-collide path.  The compiler never
@@ -116,32 +135,45 @@ __device__ __forceinline__ R gX2(const ModelConst& mc, int g) {
 // operation sequence and their results agree bit for bit.
 template <class R>
 __device__ __forceinline__ R xadd(R a, R b) {
-  if constexpr (std::is_same<R, float>::value) return __fadd_rn(a, b); else return __dadd_rn(a, b);
+  if constexpr (std::is_same<R, float>::value) return __fadd_rn(a, b);
+  else if constexpr (IsPair<R>::value) return __fadd2_rn(a, b);
+  else return __dadd_rn(a, b);
 }
 template <class R>
 __device__ __forceinline__ R xsub(R a, R b) {
-  if constexpr (std::is_same<R, float>::value) return __fsub_rn(a, b); else return __dsub_rn(a, b);
+  if constexpr (std::is_same<R, float>::value) return __fsub_rn(a, b);
+  else if constexpr (IsPair<R>::value) return __fadd2_rn(a, make_float2(-b.x, -b.y));
+  else return __dsub_rn(a, b);
 }
 template <class R>
 __device__ __forceinline__ R xmul(R a, R b) {
-  if constexpr (std::is_same<R, float>::value) return __fmul_rn(a, b); else return __dmul_rn(a, b);
+  if constexpr (std::is_same<R, float>::value) return __fmul_rn(a, b);
+  else if constexpr (IsPair<R>::value) return __fmul2_rn(a, b);
+  else return __dmul_rn(a, b);
 }
 template <class R>
 __device__ __forceinline__ R xfma(R a, R b, R c) {
-  if constexpr (std::is_same<R, float>::value) return __fmaf_rn(a, b, c); else return __fma_rn(a, b, c);
+  if constexpr (std::is_same<R, float>::value) return __fmaf_rn(a, b, c);
+  else if constexpr (IsPair<R>::value) return __ffma2_rn(a, b, c);
+  else return __fma_rn(a, b, c);
 }
-
-// A constant in the arithmetic type.
+// -a (exact)
 template <class R>
-__device__ __forceinline__ R cst(double v) {
-  return (R)v;
+__device__ __forceinline__ R xneg(R a) {
+  if constexpr (IsPair<R>::value) return make_float2(-a.x, -a.y); else return -a;
+}
+// 1 / a by the hardware approximation (per lane)
+__device__ __forceinline__ float xrcp_approx(float a) { return __fdividef(1.0f, a); }
+__device__ __forceinline__ float2 xrcp_approx(float2 a) {
+  return make_float2(__fdividef(1.0f, a.x), __fdividef(1.0f, a.y));
 }
 
 // Kahan compensated accumulation: the running error is kept in c (true sum ~ s - c).
-__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
-  const float y = __fsub_rn(x, c);
-  const float t = __fadd_rn(s, y);
-  c = __fsub_rn(__fsub_rn(t, s), y);
+template <class R>
+__device__ __forceinline__ void kahan_add(R& s, R& c, R x) {
+  const R y = xsub(x, c);
+  const R t = xadd(s, y);
+  c = xsub(xsub(t, s), y);
   s = t;
 }
 
@@ -266,9 +298,10 @@ __device__ __forceinline__ HalfMoments<Rt> half_moments(Get&& hv) {
 struct FF {
   float hi, lo;
 };
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+template <class R>
+__device__ __forceinline__ void two_sum(R a, R b, R& s, R& e) {
   s = xadd(a, b);
-  const float bb = xsub(s, a);
+  const R bb = xsub(s, a);
   e = xadd(xsub(a, xsub(s, bb)), xsub(b, bb));
 }
 __device__ __forceinline__ FF ff_add(FF a, FF b) {
@@ -298,51 +331,53 @@ __device__ __forceinline__ CellState<Rt> cell_state(const HalfMoments<Rt>& A,
   constexpr int D = Model<M>::D;
   const ModelConst& mc = c_mc[M];
   CellState<Rt> c;
-  if constexpr (std::is_same<Rt, float>::value) {
-    // FP32-arithmetic forms: rho - 1 and E - D rho as double-float on the FP32 pipe
-    FF rd, ed, rho;
-    two_sum(A.rs, B.rs, rd.hi, rd.lo);
-    rd.lo = xsub(rd.lo, xadd(A.rc, B.rc));
-    two_sum(A.es, B.es, ed.hi, ed.lo);
-    ed.lo = xsub(ed.lo, xadd(A.ec, B.ec));
-    two_sum(1.0f, rd.hi, rho.hi, rho.lo);
-    rho.lo = xadd(rho.lo, rd.lo);
-    const float rho_r = xadd(rho.hi, rho.lo);
-    const float r0 = __fdividef(1.0f, rho_r);
-    const float ir = xfma(r0, xsub(xfma(-rho.hi, r0, 1.0f), xmul(rho.lo, r0)), r0);
-    const float ir_lo = xmul(ir, xsub(xfma(-rho.hi, ir, 1.0f), xmul(rho.lo, ir)));
-    const float a = gA<float>(mc);
-    const float jx = xadd(A.jx, B.jx), jy = xadd(A.jy, B.jy), jz = xadd(A.jz, B.jz);
-    const float ux = xmul(xmul(a, jx), ir), uy = xmul(xmul(a, jy), ir);
-    const float uz = (D == 3) ? xmul(xmul(a, jz), ir) : 0.0f;
+  if constexpr (!std::is_same<Rt, double>::value) {
+    // FP32-arithmetic forms (Rt = float, or float2 for two cells): rho - 1 and
+    // E - D rho as double-float (hi, lo) on the FP32 pipe
+    const Rt one = cst<Rt>(1.0), Dv = cst<Rt>(D);
+    Rt rd_hi, rd_lo, ed_hi, ed_lo, rho_hi, rho_lo;
+    two_sum(A.rs, B.rs, rd_hi, rd_lo);
+    rd_lo = xsub(rd_lo, xadd(A.rc, B.rc));
+    two_sum(A.es, B.es, ed_hi, ed_lo);
+    ed_lo = xsub(ed_lo, xadd(A.ec, B.ec));
+    two_sum(one, rd_hi, rho_hi, rho_lo);
+    rho_lo = xadd(rho_lo, rd_lo);
+    const Rt rho_r = xadd(rho_hi, rho_lo);
+    const Rt r0 = xrcp_approx(rho_r);
+    const Rt ir = xfma(r0, xsub(xfma(xneg(rho_hi), r0, one), xmul(rho_lo, r0)), r0);
+    const Rt ir_lo = xmul(ir, xsub(xfma(xneg(rho_hi), ir, one), xmul(rho_lo, ir)));
+    const Rt a = gA<Rt>(mc);
+    const Rt jx = xadd(A.jx, B.jx), jy = xadd(A.jy, B.jy), jz = xadd(A.jz, B.jz);
+    const Rt ux = xmul(xmul(a, jx), ir), uy = xmul(xmul(a, jy), ir);
+    const Rt uz = (D == 3) ? xmul(xmul(a, jz), ir) : cst<Rt>(0.0);
     c.q = xfma(ux, ux, xfma(uy, uy, xmul(uz, uz)));
     // E - D rho = ed - D rd (the product's rounding error recovered by FMA)
-    const float ph = xmul((float)D, rd.hi);
-    const float pl = xfma((float)D, rd.lo, xfma((float)D, rd.hi, -ph));
-    float sh, se;
-    two_sum(ed.hi, -ph, sh, se);
-    const float dl = xadd(se, xsub(ed.lo, pl));
-    const float dh = xadd(sh, dl);
-    const float dlo = xsub(dl, xsub(dh, sh));
+    const Rt ph = xmul(Dv, rd_hi);
+    const Rt pl = xfma(Dv, rd_lo, xfma(Dv, rd_hi, xneg(ph)));
+    Rt sh, se;
+    two_sum(ed_hi, xneg(ph), sh, se);
+    const Rt dl = xadd(se, xsub(ed_lo, pl));
+    const Rt dh = xadd(sh, dl);
+    const Rt dlo = xsub(dl, xsub(dh, sh));
     // (E - D rho) / rho as double-float, then theta - 1 = (that - |u|^2) / D
-    const float xh = xmul(dh, ir);
-    const float xl = xfma(dh, ir_lo, xfma(dlo, ir, xfma(dh, ir, -xh)));
+    const Rt xh = xmul(dh, ir);
+    const Rt xl = xfma(dh, ir_lo, xfma(dlo, ir, xfma(dh, ir, xneg(xh))));
     // v = x - q as double-float; t = v / D rounded to nearest: a product with the
     // FP32-rounded 1/D alone is biased (it rounds 1/3 up), which would heat or cool
     // every cell by a fixed fraction of an ulp per step; one FMA residual step
     // removes it
-    float vh, ve;
-    two_sum(xh, -c.q, vh, ve);
-    const float vl = xadd(ve, xl);
-    const float third = cst<float>(1.0 / D);
-    const float y = xmul(xadd(vh, vl), third);
-    c.t = xfma(xadd(xfma(-(float)D, y, vh), vl), third, y);
+    Rt vh, ve;
+    two_sum(xh, xneg(c.q), vh, ve);
+    const Rt vl = xadd(ve, xl);
+    const Rt third = cst<Rt>(1.0 / D);
+    const Rt y = xmul(xadd(vh, vl), third);
+    c.t = xfma(xadd(xfma(xneg(Dv), y, vh), vl), third, y);
     c.uax = xmul(a, ux);
     c.uay = xmul(a, uy);
     c.uaz = xmul(a, uz);
     c.rho = rho_r;
-    c.rdev = xadd(rd.hi, rd.lo);
-    const float om = cst<float>(omega);
+    c.rdev = xadd(rd_hi, rd_lo);
+    const Rt om = cst<Rt>(omega);
     c.wr = xmul(om, rho_r);
     c.wrd = xmul(om, c.rdev);
     return c;
@@ -434,15 +469,15 @@ struct FormOpts {
   static constexpr bool kExact = sizeof(S) >= 4;
 };
 
-// a3 - a6 of one cell from its gathered, decoded populations h[Q].
-template <int M, class S, class Store>
-__device__ __forceinline__ void cell_collide(const typename Codec<S>::R (&h)[Model<M>::Q],
-                                             double omega, Store&& st) {
+// a3 - a6 of one cell (Rt = float / double) or of two cells (Rt = float2, one per
+// lane) from its gathered, decoded populations: hv(I) returns direction I's value,
+// st(I, v) stores direction I's result.  The arithmetic options follow the storage
+// form S.
+template <int M, class S, class Rt, class Get, class Store>
+__device__ __forceinline__ void cell_collide_with(Get&& hv, double omega, Store&& st) {
   using Mo = Model<M>;
-  using Rt = typename Codec<S>::R;
   constexpr int NP = Mo::NP, NH = NP / 2;
   constexpr bool SH = FormOpts<S>::kShell, EX = FormOpts<S>::kExact;
-  auto hv = [&](auto I) { return h[decltype(I)::value]; };
   // a3, a4
   const HalfMoments<Rt> A = half_moments<M, Rt, 0, NH, true, SH>(hv);
   const HalfMoments<Rt> B = half_moments<M, Rt, NH, NP, false, SH>(hv);
@@ -450,6 +485,14 @@ __device__ __forceinline__ void cell_collide(const typename Codec<S>::R (&h)[Mod
   // a5, a6
   half_collide<M, Rt, 0, NH, true, EX>(c, omega, hv, st);
   half_collide<M, Rt, NH, NP, false, EX>(c, omega, hv, st);
+}
+
+// a3 - a6 of one cell from its gathered, decoded populations h[Q].
+template <int M, class S, class Store>
+__device__ __forceinline__ void cell_collide(const typename Codec<S>::R (&h)[Model<M>::Q],
+                                             double omega, Store&& st) {
+  using Rt = typename Codec<S>::R;
+  cell_collide_with<M, S, Rt>([&](auto I) { return h[decltype(I)::value]; }, omega, st);
 }
 
 // One cell update: a1 + a2 through the load functor (all Q loads issued before any

@@ -396,7 +396,8 @@ cudaError_t enqueue_steps(lbm_ctx* c, int64_t n, int variant, int* cur, cudaStre
     // Only for states of at most twice the L2 (129 MB); on large grids the reuse is
     // negligible and the descending walk measured ~1 % slower.
     const bool alt = state_bytes(c) <= ((size_t)256 << 20);
-    const int v = variant | ((alt && variant == kVariantDirect && *cur == 1) ? kStepReverse : 0);
+    const bool walks = variant == kVariantDirect || variant == kVariantPair;
+    const int v = variant | ((alt && walks && *cur == 1) ? kStepReverse : 0);
     const StepTest* t = nullptr;
     if (c->test_pending && variant == kVariantTma) {
       t = &c->test;
@@ -452,8 +453,7 @@ int do_steps(lbm_ctx* c, int64_t n) {
   const int variant = pick_variant(c);
   const int64_t per_step = c->fix_width > 0 ? 2 : 1;
   int64_t done = 0;
-  if (c->graph_steps > 0 && (variant == kVariantDirect || variant == kVariantTma) &&
-      !c->test_pending && n >= 2 * c->graph_steps &&
+  if (c->graph_steps > 0 && !c->test_pending && n >= 2 * c->graph_steps &&
       (c->graph.exec[c->cur] || capture_steps(c, c->cur, variant))) {
     for (; n - done >= c->graph_steps; done += c->graph_steps) {
       cudaError_t e = cudaGraphLaunch(c->graph.exec[c->cur], c->stream);
@@ -661,7 +661,7 @@ int lbm_set_graph_steps(lbm_ctx* c, int steps) {
   c->graph_steps = steps;
   // capture both starting buffers now, so that no later lbm_step pays for it
   const int variant = pick_variant(c);
-  if (steps > 0 && (variant == kVariantDirect || variant == kVariantTma))
+  if (steps > 0)
     for (int parity = 0; parity < 2; ++parity)
       if (!capture_steps(c, parity, variant))
         return fail(LBM_ECUDA, "graph capture of the step failed; direct launches stay in use");
@@ -671,8 +671,12 @@ int lbm_set_graph_steps(lbm_ctx* c, int steps) {
 int lbm_set_variant(lbm_ctx* c, int variant) {
   if (!c) return fail(LBM_EINVAL, "ctx is NULL");
   if (variant != 0 && variant != kVariantDirect && variant != kVariantTma &&
-      variant != kVariantSplit)
+      variant != kVariantSplit && variant != kVariantPair)
     return fail(LBM_EINVAL, "variant %d", variant);
+  if (variant == kVariantPair && c->ops->elem_bytes != 2)
+    return fail(LBM_EINVAL, "the pair kernel is for the FP16 / BF16 forms");
+  if (variant == kVariantPair && !pair_applicable(c->g))
+    return fail(LBM_EINVAL, "the pair kernel needs Nx even");
   if (variant == kVariantSplit && c->storage == LBM_FP64)
     return fail(LBM_EINVAL, "the split kernel is for the FP32-arithmetic forms");
   if (variant == kVariantTma && !tma_applicable(c->g))

@@ -1,0 +1,116 @@
+// stream_collide_pair.cuh - two cells per thread on the paired FP32 instructions
+// (sm_103a), for the FP16 / BF16 deviation forms.
+//
+// The 16-bit forms move half the bytes of the FP32 form, so one thread per cell
+// leaves them bound by instruction issue: each cell update costs ~2300
+// instructions, more than half of them FP32 arithmetic (moments, temperature,
+// equilibrium, relaxation).  Here a thread updates the two neighbouring cells
+// x and x + 1 of a row together:
+//   * every FP32 operation of cell_collide runs once on a float2 (lane .x cell x,
+//     lane .y cell x + 1) through the paired instructions (__fadd2_rn,
+//     __fmul2_rn, __ffma2_rn), each lane rounded exactly as the scalar operation,
+//     so the results are bitwise those of the one-cell kernels;
+//   * the two cells' populations of a direction are adjacent in memory: for even
+//     e_x the pair (x - e_x, x + 1 - e_x) is one aligned 32-bit load; for odd e_x
+//     it is two 16-bit loads (the second may wrap to x = 0), packed;
+//   * the Q populations stay packed (one 32-bit register per direction for both
+//     cells) and are unpacked to float2 where they are used;
+//   * each direction's two results leave as one packed, aligned 32-bit store.
+// Needs Nx even (so that x and x + 1 share a row and pairs start 4-byte aligned).
+#pragma once
+
+#include "kernels.cuh"
+
+namespace lbm {
+
+template <class S>
+struct PairCodec;
+// dec() is volatile inline PTX on purpose: each population is decoded where it is
+// used (once for the moments, once for the relaxation), so only the packed pair
+// stays live in between; a decode the compiler could merge would keep two FP32
+// registers per direction alive instead of one packed register and spill.
+template <>
+struct PairCodec<__half> {
+  using P = __half2;
+  static __device__ __forceinline__ float2 dec(P v) {
+    float2 r;
+    asm volatile("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
+                 "cvt.f32.f16 %0, lo;\n\tcvt.f32.f16 %1, hi;\n\t}"
+                 : "=f"(r.x), "=f"(r.y)
+                 : "r"(*reinterpret_cast<const uint32_t*>(&v)));
+    return r;
+  }
+  static __device__ __forceinline__ P enc(float2 v) { return __float22half2_rn(v); }
+  static __device__ __forceinline__ P make(__half lo, __half hi) { return __halves2half2(lo, hi); }
+};
+template <>
+struct PairCodec<__nv_bfloat16> {
+  using P = __nv_bfloat162;
+  static __device__ __forceinline__ float2 dec(P v) {
+    float2 r;
+    asm volatile("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
+                 "cvt.f32.bf16 %0, lo;\n\tcvt.f32.bf16 %1, hi;\n\t}"
+                 : "=f"(r.x), "=f"(r.y)
+                 : "r"(*reinterpret_cast<const uint32_t*>(&v)));
+    return r;
+  }
+  static __device__ __forceinline__ P enc(float2 v) { return __float22bfloat162_rn(v); }
+  static __device__ __forceinline__ P make(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+    return __halves2bfloat162(lo, hi);
+  }
+};
+
+constexpr int kPairThreads = 64;                  // 128 cells per block
+
+// Resident 64-thread blocks per SM the registers are capped for.
+#ifndef LBM_PAIR_MINB_D3Q95
+#define LBM_PAIR_MINB_D3Q95 6
+#endif
+#ifndef LBM_PAIR_MINB_D2Q33
+#define LBM_PAIR_MINB_D2Q33 8
+#endif
+template <int M>
+struct PairMinBlocks {
+  static constexpr int value = M == 1 ? LBM_PAIR_MINB_D3Q95 : LBM_PAIR_MINB_D2Q33;
+};
+
+// REV: walk the blocks in reverse order (see k_stream_collide).
+template <int M, class S, bool REV>
+__global__ void __launch_bounds__(kPairThreads, PairMinBlocks<M>::value)
+    k_stream_collide_pair(const S* __restrict__ src, S* __restrict__ dst, Grid g, double omega) {
+  using Mo = Model<M>;
+  using PC = PairCodec<S>;
+  using P = typename PC::P;
+  constexpr int D = Mo::D, RR = Mo::R, Q = Mo::Q;
+  wait_prior_grid();
+  allow_next_grid();
+  const int bx = REV ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x;
+  const int x = 2 * (bx * kPairThreads + (int)threadIdx.x);
+  if (x >= g.nx) return;
+  const int y = REV ? (int)(gridDim.y - 1 - blockIdx.y) : (int)blockIdx.y;
+  const int z = REV ? (int)(gridDim.z - 1 - blockIdx.z) : (int)blockIdx.z;
+  int xo[2 * RR + 1], yo[2 * RR + 1], zo[2 * RR + 1];
+  neighbour_offsets<D, RR>(x, y, z, g.nx, g.ny, g.nz, g.nxy, xo, yo, zo);
+  // a1 + a2 gather: Q packed pairs
+  P h2[Q];
+  sfor<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    constexpr int ex = Mo::vs.e[i][0], ey = Mo::vs.e[i][1], ez = Mo::vs.e[i][2];
+    const S* row = src + (size_t)i * (size_t)g.ncell + (zo[ez + RR] + yo[ey + RR]);
+    const int xs = xo[ex + RR];                    // (x - e_x) mod Nx
+    if constexpr ((ex & 1) == 0) {
+      h2[i] = __ldg(reinterpret_cast<const P*>(row + xs));   // xs even: aligned pair
+    } else {
+      const int xs1 = (xs + 1 == g.nx) ? 0 : xs + 1;       // (x + 1 - e_x) mod Nx
+      h2[i] = PC::make(__ldg(row + xs), __ldg(row + xs1));
+    }
+  });
+  const size_t self = ((size_t)z * g.ny + y) * g.nx + x;
+  cell_collide_with<M, S, float2>(
+      [&](auto I) { return PC::dec(h2[decltype(I)::value]); }, omega,
+      [&](auto I, float2 v) {
+        *reinterpret_cast<P*>(dst + (size_t)decltype(I)::value * (size_t)g.ncell + self) = PC::enc(v);
+      });
+}
+
+}  // namespace lbm

@@ -28,7 +28,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ESTATE, LBM_EDEVICE, LBM_EIO = \
     0, -1, -2, -3, -4, -5, -6, -7
-VARIANT_AUTO, VARIANT_DIRECT, VARIANT_TMA, VARIANT_SPLIT = 0, 1, 2, 3
+VARIANT_AUTO, VARIANT_DIRECT, VARIANT_TMA, VARIANT_SPLIT, VARIANT_PAIR = 0, 1, 2, 3, 4
 LBM_D2Q33, LBM_D3Q95 = 0, 1
 LBM_FP64, LBM_FP32, LBM_FP16DEV, LBM_BF16DEV = 0, 1, 2, 3
 LBM_HOST, LBM_DEVICE = 0, 1

@@ -296,8 +296,9 @@ VARIANT_GRIDS = [("D3Q95", (136, 6, 5)), ("D3Q95", (8, 3, 4)), ("D3Q95", (256, 6
 @pytest.mark.parametrize("storage", ["fp64", "fp32", "fp16", "bf16"])
 @pytest.mark.parametrize("model,dims", VARIANT_GRIDS)
 def test_kernel_variants_agree_bitwise(lbm, model, dims, storage):
-    """Direct, TMA and split (FP32-arithmetic forms) kernels compute the same
-    arithmetic in the same order: their states agree bit for bit."""
+    """Direct, TMA, split (FP32-arithmetic forms) and pair (FP16 / BF16, two cells
+    per thread on paired FP32 instructions) kernels compute the same arithmetic in
+    the same order: their states agree bit for bit."""
     mdl = get_model(model)
     rng = np.random.default_rng(7)
     shape = dims[::-1]
@@ -308,6 +309,8 @@ def test_kernel_variants_agree_bitwise(lbm, model, dims, storage):
     variants = [lbm.VARIANT_DIRECT, lbm.VARIANT_TMA]
     if storage != "fp64":
         variants.append(lbm.VARIANT_SPLIT)
+    if storage in ("fp16", "bf16"):
+        variants.append(lbm.VARIANT_PAIR)
     for variant in variants:
         lat = lbm.Lattice(model, dims, 1.7, storage)
         lbm.lbm_set_variant(lat.ctx, variant)
@@ -362,3 +365,12 @@ def test_tma_bounded_wait_runs_out_and_reports(lbm, storage):
     ref.step(5)
     assert np.array_equal(got.view(np.uint8), ref.raw().view(np.uint8))
     ref.close()
+
+
+def test_pair_variant_needs_16_bit_storage_and_even_nx(lbm):
+    for storage, dims in (("fp32", (16, 4, 4)), ("fp64", (16, 4, 4)), ("fp16", (15, 4, 4))):
+        lat = lbm.Lattice("D3Q95", dims, 1.0, storage)
+        with pytest.raises(lbm.LbmError) as ei:
+            lbm.lbm_set_variant(lat.ctx, lbm.VARIANT_PAIR)
+        assert ei.value.code == lbm.LBM_EINVAL
+        lat.close()
