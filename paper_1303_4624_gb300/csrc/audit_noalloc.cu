@@ -65,6 +65,9 @@ int setup_current_device(double** scratch) {
   ModelConst both[2] = {*m0, *m1};
   e = cudaMemcpyToSymbol(c_mc, both, sizeof both);
   if (e != cudaSuccess) return ctx_cuda_fail(e, "constant table upload");
+  const float unit[2] = {1.0f, -1.0f};
+  e = cudaMemcpyToSymbol(c_unit, unit, sizeof unit);
+  if (e != cudaSuccess) return ctx_cuda_fail(e, "constant table upload");
   const unsigned long long now = current_context_id();
   for (auto it = g_setup.begin(); it != g_setup.end();)
     it = (it->dev == dev) ? g_setup.erase(it) : it + 1;

@@ -14,6 +14,9 @@ namespace {
 using S = LBM_STORE;
 
 cudaError_t upload(const ModelConst* mc2) {
+  const float unit[2] = {1.0f, -1.0f};
+  cudaError_t e = cudaMemcpyToSymbol(c_unit, unit, sizeof unit);
+  if (e != cudaSuccess) return e;
   return cudaMemcpyToSymbol(c_mc, mc2, 2 * sizeof(ModelConst));
 }
 

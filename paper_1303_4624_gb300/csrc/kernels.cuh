@@ -35,6 +35,10 @@
 namespace lbm {
 
 static __constant__ ModelConst c_mc[2];
+// {1, -1}, written by the host with the model tables.  The paired-FP32 path adds
+// and subtracts through FMAs with these factors (see xadd): the compiler cannot
+// know their values, so it cannot merge a preceding paired multiply into the add.
+static __constant__ float c_unit[2];
 
 // ----------------------------------------------------------------- storage codecs
 template <class S>
@@ -133,16 +137,22 @@ __device__ __forceinline__ R gX2(const ModelConst& mc, int g) {
 // fuses or reorders these (unlike a * b + c, which it may contract into an FMA
 // differently in each kernel), so every kernel variant performs the identical
 // operation sequence and their results agree bit for bit.
+// Paired adds and subtracts are written as a * 1 + b and b * (-1) + a with the
+// factors read from constant memory: measured on this GPU, a paired multiply whose
+// only use is a paired add is merged into one fused multiply-add even when both are
+// written with explicit round-to-nearest, which would round once where the scalar
+// code rounds twice.  An FMA by a factor the compiler cannot see keeps the two
+// roundings (x * 1 and b * -1 are exact), at the cost of no extra instruction.
 template <class R>
 __device__ __forceinline__ R xadd(R a, R b) {
   if constexpr (std::is_same<R, float>::value) return __fadd_rn(a, b);
-  else if constexpr (IsPair<R>::value) return __fadd2_rn(a, b);
+  else if constexpr (IsPair<R>::value) return __ffma2_rn(a, make_float2(c_unit[0], c_unit[0]), b);
   else return __dadd_rn(a, b);
 }
 template <class R>
 __device__ __forceinline__ R xsub(R a, R b) {
   if constexpr (std::is_same<R, float>::value) return __fsub_rn(a, b);
-  else if constexpr (IsPair<R>::value) return __fadd2_rn(a, make_float2(-b.x, -b.y));
+  else if constexpr (IsPair<R>::value) return __ffma2_rn(b, make_float2(c_unit[1], c_unit[1]), a);
   else return __dsub_rn(a, b);
 }
 template <class R>
@@ -203,14 +213,25 @@ struct EqCoef {
   __device__ __forceinline__ R A2(R x2) const { return xfma(M1, x2, M0); }
 };
 
+// acc + K v for a compile-time integer K.  K = +-1 is written as an add or a
+// subtract (the same rounding as the FMA by +-1): the compiler turns an FMA by a
+// literal +-1 into an add anyway, and a plain paired add would then be open to the
+// merge described at xadd.
+template <int K, class R>
+__device__ __forceinline__ R xaxpy(R v, R acc) {
+  if constexpr (K == 1) return xadd(acc, v);
+  else if constexpr (K == -1) return xsub(acc, v);
+  else return xfma(cst<R>(K), v, acc);
+}
+
 // s = e . v for a compile-time integer lattice vector e.
 template <class R, int EX, int EY, int EZ>
 __device__ __forceinline__ R edot(R vx, R vy, R vz) {
   R s = cst<R>(0);
   bool first = true;
   if constexpr (EX != 0) { s = xmul(cst<R>(EX), vx); first = false; }
-  if constexpr (EY != 0) { s = first ? xmul(cst<R>(EY), vy) : xfma(cst<R>(EY), vy, s); first = false; }
-  if constexpr (EZ != 0) { s = first ? xmul(cst<R>(EZ), vz) : xfma(cst<R>(EZ), vz, s); }
+  if constexpr (EY != 0) { s = first ? xmul(cst<R>(EY), vy) : xaxpy<EY>(vy, s); first = false; }
+  if constexpr (EZ != 0) { s = first ? xmul(cst<R>(EZ), vz) : xaxpy<EZ>(vz, s); }
   return s;
 }
 
@@ -281,9 +302,9 @@ __device__ __forceinline__ HalfMoments<Rt> half_moments(Get&& hv) {
       }
     }
     const Rt tj = xmul(gW<Rt>(mc, gg), xsub(hp, hm));
-    if constexpr (ex != 0) m.jx = xfma(cst<Rt>(ex), tj, m.jx);
-    if constexpr (ey != 0) m.jy = xfma(cst<Rt>(ey), tj, m.jy);
-    if constexpr (ez != 0) m.jz = xfma(cst<Rt>(ez), tj, m.jz);
+    if constexpr (ex != 0) m.jx = xaxpy<ex>(tj, m.jx);
+    if constexpr (ey != 0) m.jy = xaxpy<ey>(tj, m.jy);
+    if constexpr (ez != 0) m.jz = xaxpy<ez>(tj, m.jz);
   });
   return m;
 }

@@ -60,11 +60,14 @@ struct PairCodec<__nv_bfloat16> {
   }
 };
 
-constexpr int kPairThreads = 64;                  // 128 cells per block
+#ifndef LBM_PAIR_THREADS
+#define LBM_PAIR_THREADS 64
+#endif
+constexpr int kPairThreads = LBM_PAIR_THREADS;     // 2 cells per thread
 
 // Resident 64-thread blocks per SM the registers are capped for.
 #ifndef LBM_PAIR_MINB_D3Q95
-#define LBM_PAIR_MINB_D3Q95 6
+#define LBM_PAIR_MINB_D3Q95 4
 #endif
 #ifndef LBM_PAIR_MINB_D2Q33
 #define LBM_PAIR_MINB_D2Q33 8
