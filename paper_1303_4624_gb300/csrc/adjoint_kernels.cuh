@@ -40,15 +40,6 @@ struct EqGrad {
   static __device__ __forceinline__ R Dt(R x2) { return (x2 - R(D + 4)) * R(0.25); }
 };
 
-// 4-byte global -> shared copy (cp.async, L1-allocating) and the wait for all of
-// this thread's outstanding copies.
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_all;" ::: "memory");
-}
 
 __device__ __forceinline__ double block_sum_128(double v, double* sh) {
   v = warp_sum(v);

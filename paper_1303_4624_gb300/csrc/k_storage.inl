@@ -125,6 +125,28 @@ cudaError_t step_tma_m(const void* src, void* dst, const Grid& g, double omega, 
                             omega, (int)nchunks, status, t);
 }
 
+// The pair kernel (16-bit forms): 64-thread blocks of 128 cells, like the direct
+// kernel's grid.
+template <int M>
+cudaError_t step_pair_m(const void* src, void* dst, const Grid& g, double omega, int rev,
+                        cudaStream_t st) {
+  const int cells = 2 * kPairThreads;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)((g.nx + cells - 1) / cells), (unsigned)g.ny, (unsigned)g.nz);
+  cfg.blockDim = dim3(kPairThreads);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (rev)
+    return cudaLaunchKernelEx(&cfg, k_stream_collide_pair<M, S, true>, static_cast<const S*>(src),
+                              static_cast<S*>(dst), g, omega);
+  return cudaLaunchKernelEx(&cfg, k_stream_collide_pair<M, S, false>, static_cast<const S*>(src),
+                            static_cast<S*>(dst), g, omega);
+}
+
 template <int M>
 cudaError_t step_m(const void* src, void* dst, const Grid& g, double omega, int variant, int* status,
                    const StepTest* test, cudaStream_t st) {
@@ -132,23 +154,7 @@ cudaError_t step_m(const void* src, void* dst, const Grid& g, double omega, int 
   variant &= ~kStepReverse;
   if (variant == kVariantTma) return step_tma_m<M>(src, dst, g, omega, status, test, st);
   if constexpr (sizeof(S) == 2) {
-    if (variant == kVariantPair) {
-      const int cells = 2 * kPairThreads;
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3((unsigned)((g.nx + cells - 1) / cells), (unsigned)g.ny, (unsigned)g.nz);
-      cfg.blockDim = dim3(kPairThreads);
-      cfg.stream = st;
-      cudaLaunchAttribute attr[1];
-      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-      attr[0].val.programmaticStreamSerializationAllowed = 1;
-      cfg.attrs = attr;
-      cfg.numAttrs = 1;
-      if (rev)
-        return cudaLaunchKernelEx(&cfg, k_stream_collide_pair<M, S, true>, static_cast<const S*>(src),
-                                  static_cast<S*>(dst), g, omega);
-      return cudaLaunchKernelEx(&cfg, k_stream_collide_pair<M, S, false>, static_cast<const S*>(src),
-                                static_cast<S*>(dst), g, omega);
-    }
+    if (variant == kVariantPair) return step_pair_m<M>(src, dst, g, omega, rev, st);
   }
   if constexpr (!std::is_same<S, double>::value) {
     if (variant == kVariantSplit) {

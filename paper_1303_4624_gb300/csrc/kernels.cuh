@@ -573,6 +573,16 @@ struct DirectMinBlocks {
                                    ? 2
                                    : (Model<M>::Q == 33 ? (sizeof(S) == 4 ? 8 : 6) : LBM_DIRECT_MINB);
 };
+// 4-byte global -> shared copy (cp.async, L1-allocating) and the wait for all of
+// this thread's outstanding copies.
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 // Launched with programmatic stream serialization: the next step's grid may be
 // scheduled while this one drains; griddepcontrol.wait holds every thread until
 // the previous grid has completed and its writes are visible (a no-op when the

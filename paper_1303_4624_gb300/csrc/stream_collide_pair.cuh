@@ -65,7 +65,9 @@ struct PairCodec<__nv_bfloat16> {
 #endif
 constexpr int kPairThreads = LBM_PAIR_THREADS;     // 2 cells per thread
 
-// Resident 64-thread blocks per SM the registers are capped for.
+// Resident 64-thread blocks per SM the registers are capped for: D2Q33 128
+// registers at 8 (16 warps per SM); D3Q95 255 at 4 (8 warps per SM; a two-cell
+// D3Q95 update does not fit fewer registers without spilling).
 #ifndef LBM_PAIR_MINB_D3Q95
 #define LBM_PAIR_MINB_D3Q95 4
 #endif
@@ -77,6 +79,7 @@ struct PairMinBlocks {
   static constexpr int value = M == 1 ? LBM_PAIR_MINB_D3Q95 : LBM_PAIR_MINB_D2Q33;
 };
 
+// The Q packed pairs stay in registers between the gather and their two uses.
 // REV: walk the blocks in reverse order (see k_stream_collide).
 template <int M, class S, bool REV>
 __global__ void __launch_bounds__(kPairThreads, PairMinBlocks<M>::value)
