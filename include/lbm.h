@@ -319,6 +319,52 @@ int lbm_release_record(lbm_ctx* ctx);
 int lbm_synchronize(lbm_ctx* ctx);
 
 /*
+ * Domain decomposition (the streaming term of the update couples neighbouring
+ * cells, so a grid split into slabs needs their boundary populations every step).
+ * A grid is split along its slowest axis (z for D3Q95, y for D2Q33) into slabs
+ * of consecutive planes; each slab is a context of its own whose state holds R
+ * ghost planes on each side of its interior planes (R = stencil reach, 5 / 4):
+ * local plane p in [0, R) is a ghost below, [R, R + n) the interior, and
+ * [R + n, n + 2R) a ghost above.  The slab steps as a periodic box over its whole
+ * local array: interior cells gather only within [0, n + 2R), never across its
+ * ends, so they update exactly as in the undivided grid provided the ghost planes
+ * hold the neighbours' populations; ghost planes are recomputed from wrapped data
+ * and are overwritten before they are read again.  After every step each slab
+ * packs, per face, the populations its neighbour across that face gathers (for
+ * every direction with component c > 0 along the axis its top c interior planes
+ * go up; c < 0 the bottom |c| planes go down: 102 plane-populations per face for
+ * D3Q95, 26 for D2Q33), the message travels by any device-to-device transport
+ * (a copy, NCCL send / recv), and the neighbour unpacks it into its ghost planes.
+ * The last slab's upper neighbour is the first slab (periodic grid).
+ *
+ * lbm_create_slab - like lbm_create for a slab whose interior is dims (with
+ *   dims[2] (D3Q95) or dims[1] (D2Q33) the slab's own number of planes, at least
+ *   R); the context's grid, and every field or population array passed to it
+ *   (lbm_init, lbm_moments, lbm_get_raw ...), has R more planes on each side along
+ *   the split axis.  lbm_record and lbm_backward refuse slab contexts.
+ * lbm_halo_info - ghost planes per side R, interior planes n, segments per
+ *   message (one segment = one direction's plane) and bytes per message.
+ * lbm_halo_pack(face) - write into the device buffer `buf` (lbm_halo_info's bytes)
+ *   the message for the neighbour across `face` (0 below, 1 above), from the
+ *   current state; lbm_halo_unpack(face) - store the message received from the
+ *   neighbour across `face` into this slab's ghost planes on that side.  Both are
+ *   ordered on the context's stream and return after enqueueing.
+ * lbm_halo_plan - the message layout (host only, needs no GPU): the `count`
+ *   (direction, local plane) pairs a slab with `interior` planes sends across
+ *   `face` (send = 1) or receives there (send = 0), in message order; segs may be
+ *   NULL to query count.  Segment j occupies elements [j P, (j + 1) P) of the
+ *   message, P = Nx Ny (D3Q95) or Nx (D2Q33).
+ * Errors: LBM_EINVAL, LBM_ESTATE (not a slab, no state), LBM_ENOMEM, LBM_ECUDA.
+ */
+int lbm_create_slab(lbm_ctx** out, int model, const int64_t dims[3], double omega, int storage,
+                    void* stream);
+int lbm_halo_info(const lbm_ctx* ctx, int* ghost, int64_t* interior, int* segments,
+                  size_t* face_bytes);
+int lbm_halo_pack(lbm_ctx* ctx, int face, void* buf);
+int lbm_halo_unpack(lbm_ctx* ctx, int face, const void* buf);
+int lbm_halo_plan(int model, int64_t interior, int face, int send, int32_t* segs, int* count);
+
+/*
  * lbm_test_stall (test hook of the failure detection; the paper has no
  * counterpart) - the next TMA stream-collide launch of this context (variant 2
  * must be selected) skips the copies of chunk `chunk` (128 cells of one x-row,

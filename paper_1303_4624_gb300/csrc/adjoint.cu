@@ -109,6 +109,7 @@ int lbm_record(lbm_ctx* ctx, int64_t nsteps, int64_t ckpt_every) {
   CtxView v = ctx_view(ctx);
   if (!v.inited || !v.fields->p) return ctx_fail(LBM_ESTATE, "lbm_record needs lbm_init first");
   if (v.fixed_ends) return ctx_fail(LBM_EINVAL, "the adjoint does not cover fixed end planes");
+  if (v.slab) return ctx_fail(LBM_EINVAL, "the adjoint does not cover slab halo exchanges");
   if (nsteps < 1 || ckpt_every < 1) return ctx_fail(LBM_EINVAL, "nsteps and ckpt_every must be >= 1");
   Record& r = *v.rec;
   r.valid = false;
@@ -169,6 +170,7 @@ int lbm_record_bounded(lbm_ctx* ctx, int64_t nsteps, int64_t max_states) {
   CtxView v = ctx_view(ctx);
   if (!v.inited || !v.fields->p) return ctx_fail(LBM_ESTATE, "lbm_record_bounded needs lbm_init first");
   if (v.fixed_ends) return ctx_fail(LBM_EINVAL, "the adjoint does not cover fixed end planes");
+  if (v.slab) return ctx_fail(LBM_EINVAL, "the adjoint does not cover slab halo exchanges");
   if (nsteps < 1 || max_states < 1) return ctx_fail(LBM_EINVAL, "nsteps and max_states must be >= 1");
   Record& r = *v.rec;
   r.valid = false;

@@ -61,6 +61,7 @@ struct CtxView {
   int variant;      // stream-collide kernel variant the context uses
   int* status;      // device status flag
   bool fixed_ends;  // fixed-state end planes active (no adjoint for them)
+  bool slab;        // a slab of a decomposed grid (no adjoint across the halo exchange)
 };
 
 int ctx_fail(int code, const char* msg);

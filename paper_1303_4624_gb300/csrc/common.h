@@ -62,6 +62,10 @@ struct StorageOps {
   // populations of template cell 0 / 1 (tmpl is [Q][2] in the storage type).
   cudaError_t (*fix_ends)(void* state, const Grid& g, int axis, int width, const void* tmpl, int Q,
                           cudaStream_t st);
+  // Halo pack (to_buf = 1: state -> buf) or unpack (0) of the (direction, plane)
+  // segments segs[2 j], segs[2 j + 1] (device array), each `plane` elements.
+  cudaError_t (*halo_copy)(void* state, void* buf, const int* segs, int nseg, long long plane,
+                           long long ncell, int to_buf, cudaStream_t st);
   // Adjoint (lambda type: FP64 for the FP64 form, FP32 otherwise).
   int adj_elem_bytes;
   // One reverse step: nu_out = (collision Jacobian)^T lambda_{n+1} with

@@ -287,6 +287,16 @@ cudaError_t fix_ends(void* state, const Grid& g, int axis, int width, const void
   return cudaGetLastError();
 }
 
+cudaError_t halo_copy(void* state, void* buf, const int* segs, int nseg, long long plane,
+                      long long ncell, int to_buf, cudaStream_t st) {
+  const long long n = (long long)nseg * plane;
+  const long long nb = (n + 255) / 256;
+  k_halo_copy<S><<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, st>>>(
+      static_cast<S*>(state), static_cast<S*>(buf), reinterpret_cast<const int2*>(segs), nseg, plane,
+      ncell, to_buf);
+  return cudaGetLastError();
+}
+
 cudaError_t init(int m, const double* rho, const double* U, const double* T, void* dst,
                  const Grid& g, cudaStream_t st) {
   return m == 0 ? init_m<0>(rho, U, T, dst, g, st) : init_m<1>(rho, U, T, dst, g, st);
@@ -311,7 +321,7 @@ cudaError_t set_f(int m, const double* f, void* dst, const Grid& g, cudaStream_t
 }  // namespace
 
 const StorageOps LBM_OPS = {(int)sizeof(S), upload,       init,      step,         prepare_tma,
-                            moments,        get_f,        set_f,     fix_ends,
+                            moments,        get_f,        set_f,     fix_ends,     halo_copy,
                             (int)sizeof(L), adjoint_step, grad_init};
 
 }  // namespace lbm

@@ -999,4 +999,23 @@ __global__ void k_fix_ends(S* __restrict__ state, Grid g, int axis, int width,
   }
 }
 
+// ----------------------------------------------------------------- slab halo copy
+// Domain decomposition along the slowest axis: `segs` lists (direction, local plane)
+// pairs; segment j occupies elements [j * plane, (j + 1) * plane) of the message.
+// to_buf: state -> message (pack), else message -> state (unpack).
+template <class S>
+__global__ void k_halo_copy(S* __restrict__ state, S* __restrict__ buf, const int2* __restrict__ segs,
+                            int nseg, long long plane, long long ncell, int to_buf) {
+  const long long n = (long long)nseg * plane;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const long long j = k / plane;
+    const long long c = k - j * plane;
+    const int2 sg = segs[j];
+    const size_t off = (size_t)sg.x * (size_t)ncell + (size_t)sg.y * (size_t)plane + (size_t)c;
+    if (to_buf) buf[k] = state[off];
+    else state[off] = buf[k];
+  }
+}
+
 }  // namespace lbm

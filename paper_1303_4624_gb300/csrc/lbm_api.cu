@@ -266,6 +266,37 @@ int ensure_uploaded(int dev) {
   return LBM_OK;
 }
 
+// ================================================================ slab halo plan
+// The (direction, local plane) segments a slab with `nl` interior planes sends
+// across `face` (0: towards lower coordinates along the split axis, 1: higher), or
+// receives there (send = 0), in direction order and, within a direction, in
+// increasing plane order, so that a sender's list and its neighbour's list for the
+// same message match entry by entry.  Local planes count from the first ghost
+// plane: ghosts [0, R), interior [R, R + nl), ghosts [R + nl, nl + 2R).  A
+// direction with component c > 0 along the split axis pulls from c planes below:
+// the sender's top c interior planes of it travel across face 1 and fill the
+// receiver's ghost planes R - c .. R - 1; c < 0 mirrors that across face 0.
+void halo_plan_host(const VelSet& vs, int64_t nl, int face, int send, std::vector<int32_t>* segs) {
+  const int axis = vs.D == 3 ? 2 : 1;
+  const int R = vs.R;
+  // directions crossing this face in this message: upwards (c > 0) for what goes
+  // out of face 1 or comes in at face 0, downwards (c < 0) otherwise
+  const bool up = (face == 1) == (send != 0);
+  segs->clear();
+  for (int i = 0; i < vs.Q; ++i) {
+    const int c = vs.e[i][axis];
+    if (up ? c <= 0 : c >= 0) continue;
+    const int a = up ? c : -c;
+    for (int m = 0; m < a; ++m) {
+      int64_t plane;
+      if (face == 1) plane = send ? R + nl - a + m : R + nl + m;
+      else plane = send ? R + m : R - a + m;
+      segs->push_back(i);
+      segs->push_back((int32_t)plane);
+    }
+  }
+}
+
 // ================================================================ allocation
 std::mutex g_alloc_mu;
 lbm_alloc_fn g_alloc = nullptr;
@@ -368,6 +399,14 @@ struct lbm_ctx {
   cudaStream_t cap_stream = nullptr;
   int64_t audit_every = 0;         // lbm_step audits after every multiple of this many steps
   double audit_host[kAuditSlots] = {0};
+  // slab of a decomposed grid (lbm_create_slab): split axis (2 z, 1 y; -1 none),
+  // interior planes, ghost planes per side, and the four segment lists
+  // [send low | send high | recv low | recv high] on the device, nseg each
+  int slab_axis = -1;
+  int64_t slab_interior = 0;
+  int slab_ghost = 0;
+  int halo_nseg = 0;
+  DevBuf halo_segs;
 };
 
 namespace {
@@ -529,6 +568,7 @@ CtxView ctx_view(lbm_ctx* c) {
   v.rec = &c->rec;
   v.variant = pick_variant(c);
   v.fixed_ends = c->fix_width > 0;
+  v.slab = c->slab_axis >= 0;
   v.status = static_cast<int*>(c->status.p);
   return v;
 }
@@ -1054,6 +1094,109 @@ int lbm_synchronize(lbm_ctx* c) {
     return fail(LBM_EDEVICE, "a TMA stream-collide launch timed out waiting for its copies");
   }
   return LBM_OK;
+}
+
+// ---------------------------------------------------------------- slabs of a decomposed grid
+int lbm_halo_plan(int model, int64_t interior, int face, int send, int32_t* segs, int* count) {
+  if (model != LBM_D2Q33 && model != LBM_D3Q95) return fail(LBM_EINVAL, "unknown model %d", model);
+  if (face != 0 && face != 1) return fail(LBM_EINVAL, "face must be 0 or 1");
+  if (!count) return fail(LBM_EINVAL, "count is NULL");
+  const HostModel* hm = host_model(model);
+  if (!hm) return fail(LBM_EINVAL, "model table solve failed");
+  if (interior < hm->vs.R)
+    return fail(LBM_EINVAL, "a slab needs at least the stencil reach (%d) of interior planes", hm->vs.R);
+  std::vector<int32_t> v;
+  halo_plan_host(hm->vs, interior, face, send, &v);
+  const int n = (int)(v.size() / 2);
+  if (segs) {
+    if (*count < n) {
+      *count = n;
+      return fail(LBM_EINVAL, "segs holds %d segments, the plan has %d", *count, n);
+    }
+    std::memcpy(segs, v.data(), v.size() * sizeof(int32_t));
+  }
+  *count = n;
+  return LBM_OK;
+}
+
+int lbm_create_slab(lbm_ctx** out, int model, const int64_t dims[3], double omega, int storage,
+                    void* stream) {
+  if (!out) return fail(LBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!dims) return fail(LBM_EINVAL, "dims is NULL");
+  if (model != LBM_D2Q33 && model != LBM_D3Q95) return fail(LBM_EINVAL, "unknown model %d", model);
+  const HostModel* hm = host_model(model);
+  if (!hm) return fail(LBM_EINVAL, "model table solve failed");
+  const int axis = hm->vs.D == 3 ? 2 : 1;
+  const int R = hm->vs.R;
+  if (dims[axis] < R)
+    return fail(LBM_EINVAL, "a slab needs at least the stencil reach (%d) of interior planes", R);
+  int64_t full[3] = {dims[0], dims[1], dims[2]};
+  full[axis] += 2 * R;
+  lbm_ctx* c = nullptr;
+  int rc = lbm_create(&c, model, full, omega, storage, stream);
+  if (rc) return rc;
+  c->slab_axis = axis;
+  c->slab_interior = dims[axis];
+  c->slab_ghost = R;
+  std::vector<int32_t> all, v;
+  int nseg = -1;
+  for (int list = 0; list < 4; ++list) {   // send low, send high, recv low, recv high
+    halo_plan_host(hm->vs, dims[axis], list & 1, list < 2, &v);
+    if (nseg < 0) nseg = (int)(v.size() / 2);
+    if ((int)(v.size() / 2) != nseg) {
+      lbm_destroy(c);
+      return fail(LBM_EINVAL, "halo lists differ in length");
+    }
+    all.insert(all.end(), v.begin(), v.end());
+  }
+  c->halo_nseg = nseg;
+  DeviceGuard dg(c->dev);
+  if ((rc = c->halo_segs.ensure(all.size() * sizeof(int32_t), c->stream))) {
+    lbm_destroy(c);
+    return rc;
+  }
+  cudaError_t e = cudaMemcpyAsync(c->halo_segs.p, all.data(), all.size() * sizeof(int32_t),
+                                  cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    lbm_destroy(c);
+    return cuda_fail(e, "halo plan upload");
+  }
+  *out = c;
+  return LBM_OK;
+}
+
+int lbm_halo_info(const lbm_ctx* c, int* ghost, int64_t* interior, int* segments, size_t* face_bytes) {
+  if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+  if (c->slab_axis < 0) return fail(LBM_ESTATE, "not a slab context (lbm_create_slab)");
+  const long long plane = c->slab_axis == 2 ? (long long)c->g.nxy : (long long)c->g.nx;
+  if (ghost) *ghost = c->slab_ghost;
+  if (interior) *interior = c->slab_interior;
+  if (segments) *segments = c->halo_nseg;
+  if (face_bytes) *face_bytes = (size_t)c->halo_nseg * (size_t)plane * (size_t)c->ops->elem_bytes;
+  return LBM_OK;
+}
+
+static int halo_move(lbm_ctx* c, int face, void* buf, int to_buf) {
+  if (!c || !buf) return fail(LBM_EINVAL, "ctx or buf is NULL");
+  if (c->slab_axis < 0) return fail(LBM_ESTATE, "not a slab context (lbm_create_slab)");
+  if (face != 0 && face != 1) return fail(LBM_EINVAL, "face must be 0 or 1");
+  if (!c->inited) return fail(LBM_ESTATE, "no state yet");
+  DeviceGuard dg(c->dev);
+  const long long plane = c->slab_axis == 2 ? (long long)c->g.nxy : (long long)c->g.nx;
+  const int list = to_buf ? face : 2 + face;
+  const int* segs = static_cast<const int*>(c->halo_segs.p) + (size_t)list * 2 * c->halo_nseg;
+  cudaError_t e = c->ops->halo_copy(c->state[c->cur].p, buf, segs, c->halo_nseg, plane, c->g.ncell,
+                                    to_buf, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, to_buf ? "halo pack launch" : "halo unpack launch");
+  c->launches += 1;
+  return LBM_OK;
+}
+
+int lbm_halo_pack(lbm_ctx* c, int face, void* buf) { return halo_move(c, face, buf, 1); }
+int lbm_halo_unpack(lbm_ctx* c, int face, const void* buf) {
+  return halo_move(c, face, const_cast<void*>(buf), 0);
 }
 
 int lbm_test_stall(lbm_ctx* c, int64_t chunk, int64_t limit_ns) {

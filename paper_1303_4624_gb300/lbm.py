@@ -47,7 +47,8 @@ SYMBOLS = ("lbm_model_info", "lbm_set_allocator", "lbm_create", "lbm_destroy", "
            "lbm_moments", "lbm_audit",
            "lbm_get_populations", "lbm_set_populations", "lbm_get_raw", "lbm_set_raw",
            "lbm_record", "lbm_record_bounded", "lbm_backward", "lbm_release_record", "lbm_synchronize",
-           "lbm_launch_count", "lbm_test_stall", "lbm_audit_noalloc", "lbm_equation_count", "lbm_generate_model",
+           "lbm_launch_count", "lbm_test_stall", "lbm_create_slab", "lbm_halo_info",
+           "lbm_halo_pack", "lbm_halo_unpack", "lbm_halo_plan", "lbm_audit_noalloc", "lbm_equation_count", "lbm_generate_model",
            "lbm_strerror", "lbm_last_error")
 
 _vp, _i, _i64, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
@@ -83,6 +84,12 @@ _sig = {
     "lbm_synchronize": (_i, [_vp]),
     "lbm_launch_count": (_i64, [_vp]),
     "lbm_test_stall": (_i, [_vp, _i64, _i64]),
+    "lbm_create_slab": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(_i64), _d, _i, _vp]),
+    "lbm_halo_info": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i64), ctypes.POINTER(_i),
+                           ctypes.POINTER(ctypes.c_size_t)]),
+    "lbm_halo_pack": (_i, [_vp, _i, _vp]),
+    "lbm_halo_unpack": (_i, [_vp, _i, _vp]),
+    "lbm_halo_plan": (_i, [_i, _i64, _i, _i, _vp, ctypes.POINTER(_i)]),
     "lbm_audit_noalloc": (_i, [_i, _i, ctypes.POINTER(_i64), _vp, ctypes.c_size_t, _vp, _vp]),
     "lbm_equation_count": (_i, [_i, _i, ctypes.POINTER(_i64)]),
     "lbm_generate_model": (_i, [_i, _i, _i, _vp, _i, _i, ctypes.POINTER(_i), _vp, _vp,
@@ -216,6 +223,58 @@ def lbm_create(model, dims, omega, storage, stream=None, torch_allocator=True):
     _check(_lib.lbm_create(ctypes.byref(h), MODELS.get(model, model), d, float(omega),
                            STORAGES.get(storage, storage), stream), "lbm_create")
     return h.value
+
+
+def lbm_create_slab(model, dims, omega, storage, stream=None, torch_allocator=True):
+    """Create the context of one slab of a grid split along its slowest axis; dims are
+    the slab's interior extents (see include/lbm.h).  Returns its handle."""
+    import torch
+    if torch_allocator:
+        _install_torch_allocator()
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    h = _vp()
+    d = (_i64 * 3)(*[int(x) for x in dims])
+    _check(_lib.lbm_create_slab(ctypes.byref(h), MODELS.get(model, model), d, float(omega),
+                                STORAGES.get(storage, storage), stream), "lbm_create_slab")
+    return h.value
+
+
+def lbm_halo_info(ctx):
+    """dict(ghost, interior, segments, face_bytes) of a slab context."""
+    g, n, sg, b = _i(), _i64(), _i(), ctypes.c_size_t()
+    _check(_lib.lbm_halo_info(ctx, ctypes.byref(g), ctypes.byref(n), ctypes.byref(sg), ctypes.byref(b)),
+           "lbm_halo_info")
+    return {"ghost": g.value, "interior": n.value, "segments": sg.value, "face_bytes": b.value}
+
+
+def lbm_halo_pack(ctx, face, buf):
+    p, w = _ptr(buf)
+    if w != LBM_DEVICE:
+        raise ValueError("halo messages live in device memory")
+    _check(_lib.lbm_halo_pack(ctx, int(face), p), "lbm_halo_pack")
+
+
+def lbm_halo_unpack(ctx, face, buf):
+    p, w = _ptr(buf)
+    if w != LBM_DEVICE:
+        raise ValueError("halo messages live in device memory")
+    _check(_lib.lbm_halo_unpack(ctx, int(face), p), "lbm_halo_unpack")
+
+
+def lbm_halo_plan(model, interior, face, send):
+    """[count, 2] int32 array of (direction, local plane) segments, in message order
+    (host only, needs no GPU)."""
+    m = MODELS.get(model, model)
+    n = _i(0)
+    _check(_lib.lbm_halo_plan(m, int(interior), int(face), int(bool(send)), None, ctypes.byref(n)),
+           "lbm_halo_plan")
+    out = np.zeros((n.value, 2), dtype=np.int32)
+    _check(_lib.lbm_halo_plan(m, int(interior), int(face), int(bool(send)), out.ctypes.data,
+                              ctypes.byref(n)), "lbm_halo_plan")
+    return out
 
 
 def lbm_destroy(ctx):
