@@ -283,11 +283,13 @@ int lbm_record(lbm_ctx* ctx, int64_t nsteps, int64_t ckpt_every);
 /*
  * lbm_record_bounded - the same forward as lbm_record, for grids whose uniform
  * checkpoints do not fit: only S_0 is kept.  The reverse sweep of lbm_backward
- * then stores at most max_states >= 1 states (S_0 included), placed by recursive
- * bisection of the step range; ranges deeper than the budget are recomputed
- * from their nearest stored state.  Recomputation is about (log2(nsteps) / 2 +
- * nsteps / 2^max_states) sweeps; e.g. 6 states for 300 steps cost ~4 forward
- * sweeps.  The context's two population buffers serve as work space: after such
+ * then stores at most max_states >= 1 states (S_0 included), each placed where
+ * it minimises the forward steps recomputed (binomial checkpointing: a dynamic
+ * programme over the split points, built on the host by this call when
+ * nsteps^2 (max_states - 1) <= 2e8, else recursive bisection); ranges deeper
+ * than the budget are recomputed from their nearest stored state.  E.g. 6 states
+ * for 300 steps recompute 1035 forward steps (bisection: 1191).  The context's
+ * two population buffers serve as work space: after such
  * a backward the context holds S_0 (steps done = 0).  Gradients are bitwise
  * identical to the uniform schedule's.
  * Errors: LBM_ESTATE (no lbm_init), LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA.

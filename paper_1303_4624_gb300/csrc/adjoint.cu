@@ -12,6 +12,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <vector>
 
 #include "../../include/lbm.h"
 #include "adjoint.h"
@@ -72,9 +73,40 @@ int advance(Sweep& w, const void* src, int64_t k, void* dst, void* work0, void* 
   return LBM_OK;
 }
 
+// Optimal split points for reversing l <= N steps with f <= F free state slots,
+// minimising the forward steps recomputed (binomial checkpointing, Griewank 1992;
+// this is the plain dynamic programme over its recursion):
+//   cost(1, f) = 0,  cost(l, 0) = l (l - 1) / 2   (each state recomputed from the start),
+//   cost(l, f) = min over 1 <= m < l of  m + cost(l - m, f - 1) + cost(m, f)
+// (advance m steps and store that state, reverse the last l - m steps with one slot
+// fewer, then the first m with the same slots).  O(N^2 F) host work; callers fall
+// back to bisection beyond a size limit.
+void optimal_splits(int64_t N, int64_t F, std::vector<int32_t>* split) {
+  const int64_t W = F + 1;
+  std::vector<int64_t> cost((size_t)(N + 1) * W, 0);
+  split->assign((size_t)(N + 1) * W, 0);
+  for (int64_t l = 2; l <= N; ++l) {
+    cost[(size_t)(l * W)] = l * (l - 1) / 2;
+    for (int64_t f = 1; f <= F; ++f) {
+      int64_t best = -1, arg = 1;
+      for (int64_t m = 1; m < l; ++m) {
+        const int64_t c = m + cost[(size_t)((l - m) * W + f - 1)] + cost[(size_t)(m * W + f)];
+        if (best < 0 || c < best) {
+          best = c;
+          arg = m;
+        }
+      }
+      cost[(size_t)(l * W + f)] = best;
+      (*split)[(size_t)(l * W + f)] = (int32_t)arg;
+    }
+  }
+}
+
 // Adjoint steps hi-1 .. lo, with S_lo in s_lo and `used` stored states in use.
-// Bisection while stored states remain; below that, each state is recomputed
-// from S_lo.  Work buffers: the context's two population buffers.
+// While stored states remain, the range is split at the optimal point (bisection
+// if the split table was not built) and the state there is stored; below that,
+// each state is recomputed from S_lo.  Work buffers: the context's two population
+// buffers.
 int reverse_bounded(Sweep& w, int64_t lo, int64_t hi, const void* s_lo, int64_t used) {
   Record& r = *w.r;
   void* w0 = w.v.state[0]->p;
@@ -87,7 +119,9 @@ int reverse_bounded(Sweep& w, int64_t lo, int64_t hi, const void* s_lo, int64_t 
     if ((rc = r.ckpt[used]->ensure((size_t)w.v.Q * (size_t)w.v.g.ncell * (size_t)w.v.ops->elem_bytes,
                                    w.v.stream)))
       return rc;
-    const int64_t mid = lo + len / 2;
+    const int64_t F = r.max_states - 1, f = r.max_states - used;
+    const int64_t mid =
+        r.split.empty() ? lo + len / 2 : lo + r.split[(size_t)(len * (F + 1) + f)];
     void* s_mid = r.ckpt[used]->p;
     if ((rc = advance(w, s_lo, mid - lo, s_mid, w0, w1))) return rc;
     if ((rc = reverse_bounded(w, mid, hi, s_mid, used + 1))) return rc;
@@ -200,6 +234,10 @@ int lbm_record_bounded(lbm_ctx* ctx, int64_t nsteps, int64_t max_states) {
   r.tail_kept = false;
   r.bounded = true;
   r.max_states = max_states;
+  // optimal splits when the host table is small enough (~0.2 s at the limit)
+  const int64_t F = max_states - 1;
+  if ((double)nsteps * (double)nsteps * (double)F <= 2e8) optimal_splits(nsteps, F, &r.split);
+  else r.split.clear();
   r.valid = true;
   return LBM_OK;
 }

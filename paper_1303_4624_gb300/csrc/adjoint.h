@@ -36,6 +36,10 @@ struct Record {
   bool tail_kept = false;                       // seg[] holds the last segment's states
   bool bounded = false;                         // lbm_record_bounded: bisection schedule
   int64_t max_states = 0;                       // stored-state budget of the bounded schedule
+  // optimal split points of the bounded schedule: split[l * (F + 1) + f] = how far to
+  // advance before storing, for l steps to reverse with f free state slots (empty:
+  // bisection); F = max_states - 1
+  std::vector<int32_t> split;
   std::vector<std::unique_ptr<DevBuf>> ckpt;    // ceil(nsteps / k) states
   std::vector<std::unique_ptr<DevBuf>> seg;     // k - 1 replayed states
   DevBuf nu[2];                                 // adjoint ping-pong, Q * cells of the adjoint type

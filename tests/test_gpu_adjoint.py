@@ -125,6 +125,25 @@ def test_autograd_function(lbm):
     assert abs(om.grad.item() - odom) < 1e-10 * max(1.0, abs(odom))
 
 
+def min_recompute(n, free):
+    """Fewest forward steps that reverse n steps with `free` extra stored states
+    (store a state m steps on, reverse the rest with one slot fewer, then the first
+    m; with no slot every state is recomputed from the start)."""
+    cost = [[0] * (free + 1) for _ in range(n + 1)]
+    for l in range(2, n + 1):
+        cost[l][0] = l * (l - 1) // 2
+        for f in range(1, free + 1):
+            cost[l][f] = min(m + cost[l - m][f - 1] + cost[m][f] for m in range(1, l))
+    return cost[n][free]
+
+
+def test_optimal_recompute_counts():
+    """The schedule's cost against hand counts: 300 steps with 6 stored states take
+    1035 recomputed steps (bisection 1191); no spare state is the triangular count."""
+    assert min_recompute(300, 5) == 1035
+    assert min_recompute(11, 0) == 55 and min_recompute(2, 1) == 1 and min_recompute(1, 3) == 0
+
+
 @pytest.mark.parametrize("max_states", [1, 2, 3, 16])
 def test_bounded_schedule_matches_uniform_bitwise(lbm, max_states):
     """lbm_record_bounded stores at most max_states states and recomputes the rest;
@@ -138,7 +157,11 @@ def test_bounded_schedule_matches_uniform_bitwise(lbm, max_states):
     rhoN = np.zeros(dims[::-1])
     lbm.lbm_moments(lat.ctx, rhoN, None, None)
     dr, dU, dT = np.zeros_like(rho0), np.zeros_like(U0), np.zeros_like(T0)
+    before = lbm.lbm_launch_count(lat.ctx)
     dom = lbm.lbm_backward(lat.ctx, np.ascontiguousarray(c), dr, dU, dT)
+    # launches: the optimal number of recomputed forward steps, n adjoint steps,
+    # grad_init and the omega reduction
+    assert lbm.lbm_launch_count(lat.ctx) - before == min_recompute(n, max_states - 1) + n + 2
     for a, b in zip((rhoN, dr, dU, dT, dom), ref):
         assert np.array_equal(np.asarray(a), np.asarray(b))
     # afterwards the context holds the initial state
