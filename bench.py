@@ -514,7 +514,8 @@ def large_leg(lbm, W, stream, steps=300):
                           "dL_drho0_rms": float(d_rho.pow(2).mean().sqrt()),
                           "max_states": max_states, "forward_s": round(fw, 3),
                           "backward_s": round(bw, 3), "backward_over_forward": round(bw / fw, 2),
-                          "schedule": "bisection over %d stored FP16 states" % max_states}
+                          "schedule": "%d stored FP16 states (S_0 included), placed to "
+                                      "minimise the recomputed steps" % max_states}
         del target, rhoN, g, d_rho
     lbm.lbm_release_record(lat.ctx)
     lat.close()

@@ -287,8 +287,9 @@ int lbm_record(lbm_ctx* ctx, int64_t nsteps, int64_t ckpt_every);
  * it minimises the forward steps recomputed (binomial checkpointing: a dynamic
  * programme over the split points, built on the host by this call when
  * nsteps^2 (max_states - 1) <= 2e8, else recursive bisection); ranges deeper
- * than the budget are recomputed from their nearest stored state.  E.g. 6 states
- * for 300 steps recompute 1035 forward steps (bisection: 1191).  The context's
+ * than the budget are recomputed from their nearest stored state.  E.g. 7 states
+ * (S_0 and 6 more) for 300 steps recompute 1035 forward steps (bisection: 1191).
+ * The context's
  * two population buffers serve as work space: after such
  * a backward the context holds S_0 (steps done = 0).  Gradients are bitwise
  * identical to the uniform schedule's.

@@ -138,9 +138,10 @@ def min_recompute(n, free):
 
 
 def test_optimal_recompute_counts():
-    """The schedule's cost against hand counts: 300 steps with 6 stored states take
-    1035 recomputed steps (bisection 1191); no spare state is the triangular count."""
-    assert min_recompute(300, 5) == 1035
+    """The schedule's cost against hand counts: 300 steps with 7 stored states (S_0
+    and 6 more) take 1035 recomputed steps (bisection 1191), with 6 states 1170
+    (bisection 1249); no spare state is the triangular count."""
+    assert min_recompute(300, 6) == 1035 and min_recompute(300, 5) == 1170
     assert min_recompute(11, 0) == 55 and min_recompute(2, 1) == 1 and min_recompute(1, 3) == 0
 
 
