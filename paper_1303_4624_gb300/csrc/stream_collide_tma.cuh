@@ -19,10 +19,11 @@
 //   * Every thread reads its Q populations from the stage at compile-time offsets
 //     (row offset + 8 - e_x, or - e_x, plus its lane): no address arithmetic, no
 //     periodic wrap in the inner loop.
-//   * OUT_SMEM (16-bit forms): the Q results of the chunk go to a shared-memory
-//     output tile, and warp 0 writes each direction's 128 results back with one
-//     bulk copy (shared -> global), so the stores need no address arithmetic
-//     either.  Otherwise each thread stores straight to global memory.
+//   * OUT_SMEM (used for the D2Q33 16-bit forms): the Q results of the chunk go to
+//     a shared-memory output tile, and warp 0 writes each direction's 128 results
+//     back with one bulk copy (shared -> global), so the stores need no address
+//     arithmetic either.  Otherwise each thread stores straight to global memory
+//     (measured faster for D3Q95: the tile costs two block barriers per chunk).
 //
 // Every wait is bounded (limit_ns of wall time): a timeout sets *status (read by
 // lbm_synchronize as LBM_EDEVICE), the CTA stops, and warp 0 waits (bounded) for

@@ -334,17 +334,20 @@ def test_tma_variant_needs_nx_multiple_of_8(lbm):
     lat.close()
 
 
-@pytest.mark.parametrize("storage", ["fp16", "fp32"])
-def test_tma_bounded_wait_runs_out_and_reports(lbm, storage):
+@pytest.mark.parametrize("model,dims,storage", [("D3Q95", (256, 64, 32), "fp16"),
+                                                ("D3Q95", (256, 64, 32), "fp32"),
+                                                ("D2Q33", (2048, 64, 1), "fp16")])
+def test_tma_bounded_wait_runs_out_and_reports(lbm, model, dims, storage):
     """Failure detection of the TMA kernel without a fault: the test hook makes the
     producer skip one chunk's copies, so that chunk's consumers wait for data that
     never comes; their wait gives up after 20 ms, the CTA stops (after waiting for
     its other copies in flight), and lbm_synchronize reports LBM_EDEVICE once.  The
     context stays usable: a fresh run on it matches the direct kernel bit for bit.
-    FP16 covers the path with the shared-memory output tile, FP32 the direct stores."""
-    dims = (256, 64, 32)
-    fields = W.riemann_planar(3, *dims, 128, (1.0, 1.0), (0.6, 0.75), seed=9)
-    lat = lbm.Lattice("D3Q95", dims, 1.6, storage)
+    D2Q33 FP16 covers the path with the shared-memory output tile and bulk stores,
+    the D3Q95 forms the path that stores from the threads."""
+    D = 3 if model == "D3Q95" else 2
+    fields = W.riemann_planar(D, *dims, dims[0] // 2, (1.0, 1.0), (0.6, 0.75), seed=9)
+    lat = lbm.Lattice(model, dims, 1.6, storage)
     lbm.lbm_set_graph_steps(lat.ctx, 0)
     lbm.lbm_set_variant(lat.ctx, lbm.VARIANT_TMA)
     lat.init(fields.rho, fields.U, fields.theta * lat.info["T0"])
@@ -359,7 +362,7 @@ def test_tma_bounded_wait_runs_out_and_reports(lbm, storage):
     lbm.lbm_synchronize(lat.ctx)
     got = lat.raw()
     lat.close()
-    ref = lbm.Lattice("D3Q95", dims, 1.6, storage)
+    ref = lbm.Lattice(model, dims, 1.6, storage)
     lbm.lbm_set_variant(ref.ctx, lbm.VARIANT_DIRECT)
     ref.init(fields.rho, fields.U, fields.theta * ref.info["T0"])
     ref.step(5)
