@@ -142,7 +142,8 @@ class ClockSampler:
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for fn in ("kernels.cuh", "velset.cuh", "k_storage.inl", "common.h"):
+    for fn in ("kernels.cuh", "velset.cuh", "k_storage.inl", "common.h", "stream_collide_tma.cuh",
+               "stream_collide_pair.cuh"):
         with open(os.path.join(ROOT, "paper_1303_4624_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
