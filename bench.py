@@ -479,10 +479,17 @@ def large_leg(lbm, W, stream, steps=300):
     lat = make_lattice(lbm, wl, fields)
     dt = time_steps(lbm, lat, steps, 5, stream)
     a = lat.audit()
+    key = "precision_d3q95_oblique_96x48x48_300"
+    err = profile_record(key, "fp16_rho")
     out = {"workload": wl.name, "storage": "fp16", "steps": steps,
            "mlups": round(wl.cells * steps / dt / 1e6, 1),
            "gbs": round(wl.cells * 2 * 95 * 2 / (dt / steps) / 1e9, 1),
-           "nonfinite_after": a["nonfinite"]}
+           "nonfinite_after": a["nonfinite"],
+           "error_vs_fp64_oracle": None if err is None else
+           {"rho": err, "T": profile_record(key, "fp16_T"),
+            "source": "300 steps of the same setup (without density noise) on the 96x48x48 "
+                      "stand-in grid, tests/test_gpu_precision.py, recorded in "
+                      "profiles/precision_forms_d3q95_128x32x32.md for this kernel source"}}
     # adjoint of L = mean (rho_N - rho*)^2
     state_b = wl.cells * 95 * 2
     lam_b = 2 * wl.cells * 95 * 4
