@@ -28,7 +28,8 @@
  *     host output return after the result is on the host; calls with device
  *     outputs (and lbm_step) return after enqueueing.
  *   - Every call returns LBM_OK (0) or a negative error code; arguments are
- *     validated on the host before anything is launched.  lbm_last_error()
+ *     validated before any launch that uses them (on the host, except the
+ *     initial fields of lbm_init, checked on the device after their upload).  lbm_last_error()
  *     gives a message for the most recent failure on the calling thread.
  */
 #ifndef LBM_GB300_H
@@ -181,10 +182,13 @@ int lbm_set_stream(lbm_ctx* ctx, void* stream);
  * with m = N = 4, in the dimensionless variables theta = T / T0, u = c U
  * defined after the Maxwellian.
  *   rho [cells], U [D][cells] (lattice units), T [cells] (lattice units),
- *   all FP64 in `where` memory.  rho > 0 and T > 0 and all values finite
- *   (checked on the host for LBM_HOST; for LBM_DEVICE inputs the values are
- *   not inspected).  The fields are also kept on the device as the initial
- *   state of the differentiable rollout (lbm_record / lbm_backward).
+ *   all FP64 in `where` memory.  rho > 0 and T > 0 and all values finite:
+ *   for LBM_HOST inputs this is checked on the device right after the upload
+ *   (one pass at HBM speed, then one blocking read of the result), before the
+ *   equilibrium is launched; a refused call leaves the populations as they were
+ *   but invalidates a recorded rollout.  LBM_DEVICE inputs are not inspected
+ *   (the call stays asynchronous).  The fields are also kept on the device as the
+ *   initial state of the differentiable rollout (lbm_record / lbm_backward).
  * Errors: LBM_EINVAL, LBM_ECUDA.
  */
 int lbm_init(lbm_ctx* ctx, const double* rho, const double* U, const double* T, int where);

@@ -86,6 +86,10 @@ inline long long cell_blocks(const Grid& g) {
   return (long long)((g.nx + bx - 1) / bx) * g.ny * g.nz;
 }
 cudaError_t launch_sum_reduce(const double* partials, long long n, double* out, cudaStream_t st);
+// *first_bad = min over bad values of (index << 2 | field) (0 rho, 1 U, 2 T); the
+// caller presets it to all ones.
+cudaError_t launch_check_fields(const double* rho, const double* U, const double* T, long long n,
+                                int D, unsigned long long* first_bad, cudaStream_t st);
 
 extern const StorageOps kOpsFP64, kOpsFP32, kOpsFP16, kOpsBF16;
 

@@ -12,6 +12,33 @@ cudaError_t launch_audit_reduce(const double* partials, int nblocks, double* out
   k_audit_reduce<<<1, 256, 0, st>>>(partials, nblocks, out);
   return cudaGetLastError();
 }
+// Validation of the initial fields on the device: rho > 0, T > 0 and every value
+// finite (NaN fails every comparison).  *first_bad (preset to all ones) receives the
+// smallest (index << 2 | field) of a bad value, field 0 rho, 1 U, 2 T.
+static __global__ void k_check_fields(const double* __restrict__ rho, const double* __restrict__ U,
+                                      const double* __restrict__ T, long long n, int D,
+                                      unsigned long long* __restrict__ first_bad) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    int field = -1;
+    const double r = rho[i], t = T[i];
+    if (!(r > 0.0 && r <= 1.7976931348623157e308)) field = 0;
+    else {
+      for (int d = 0; d < D; ++d)
+        if (!(fabs(U[(size_t)d * n + i]) <= 1.7976931348623157e308)) field = 1;
+      if (field < 0 && !(t > 0.0 && t <= 1.7976931348623157e308)) field = 2;
+    }
+    if (field >= 0) atomicMin(first_bad, ((unsigned long long)i << 2) | (unsigned long long)field);
+  }
+}
+
+cudaError_t launch_check_fields(const double* rho, const double* U, const double* T, long long n,
+                                int D, unsigned long long* first_bad, cudaStream_t st) {
+  const long long nb = (n + 255) / 256;
+  k_check_fields<<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, st>>>(rho, U, T, n, D, first_bad);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sum_reduce(const double* partials, long long n, double* out, cudaStream_t st) {
   k_sum_reduce<<<1, 256, 0, st>>>(partials, n, out);
   return cudaGetLastError();

@@ -385,6 +385,7 @@ struct lbm_ctx {
   DevBuf partials;    // audit block partials
   DevBuf audit_out;   // 8 doubles
   DevBuf status;      // device int: 1 after a kernel gave up on a bounded wait
+  DevBuf check;       // device word: first invalid initial field value (lbm_init)
   int variant = 0;    // 0 auto, kVariantDirect, kVariantTma, kVariantSplit
   StepTest test{-1, 0};  // lbm_test_stall: applies to the next TMA launch only
   bool test_pending = false;
@@ -791,13 +792,6 @@ int lbm_init(lbm_ctx* c, const double* rho, const double* U, const double* T, in
   if (!rho || !U || !T) return fail(LBM_EINVAL, "rho, U and T are required");
   if (where != LBM_HOST && where != LBM_DEVICE) return fail(LBM_EINVAL, "bad where");
   const size_t n = (size_t)c->g.ncell;
-  if (where == LBM_HOST) {
-    for (size_t k = 0; k < n; ++k)
-      if (!(std::isfinite(rho[k]) && rho[k] > 0.0)) return fail(LBM_EINVAL, "rho[%zu] = %g", k, rho[k]);
-    for (size_t k = 0; k < n; ++k)
-      if (!(std::isfinite(T[k]) && T[k] > 0.0)) return fail(LBM_EINVAL, "T[%zu] = %g", k, T[k]);
-    if (!all_finite(U, n * c->D)) return fail(LBM_EINVAL, "U has non-finite values");
-  }
   DeviceGuard dg(c->dev);
   int rc = c->fields.ensure((size_t)(c->D + 2) * n * sizeof(double), c->stream);
   if (rc) return rc;
@@ -806,6 +800,28 @@ int lbm_init(lbm_ctx* c, const double* rho, const double* U, const double* T, in
   LBM_CUDA(cudaMemcpyAsync(f, rho, n * sizeof(double), kind, c->stream));
   LBM_CUDA(cudaMemcpyAsync(f + n, U, (size_t)c->D * n * sizeof(double), kind, c->stream));
   LBM_CUDA(cudaMemcpyAsync(f + (size_t)(c->D + 1) * n, T, n * sizeof(double), kind, c->stream));
+  if (where == LBM_HOST) {
+    // host fields are validated on the device once uploaded (a pass over them on the
+    // host costs more than the upload), before the equilibrium is launched
+    if ((rc = c->check.ensure(sizeof(unsigned long long), c->stream))) return rc;
+    LBM_CUDA(cudaMemsetAsync(c->check.p, 0xff, sizeof(unsigned long long), c->stream));
+    cudaError_t e = launch_check_fields(f, f + n, f + (size_t)(c->D + 1) * n, (long long)n, c->D,
+                                        static_cast<unsigned long long*>(c->check.p), c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "field check launch");
+    c->launches += 1;
+    unsigned long long bad = 0;
+    LBM_CUDA(cudaMemcpyAsync(&bad, c->check.p, sizeof bad, cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(cudaStreamSynchronize(c->stream));
+    if (bad != ~0ull) {
+      c->rec.valid = false;   // the kept initial fields were overwritten
+      const size_t k = (size_t)(bad >> 2);
+      switch ((int)(bad & 3)) {
+        case 0: return fail(LBM_EINVAL, "rho[%zu] = %g (rho must be finite and > 0)", k, rho[k]);
+        case 2: return fail(LBM_EINVAL, "T[%zu] = %g (T must be finite and > 0)", k, T[k]);
+        default: return fail(LBM_EINVAL, "U has a non-finite value at cell %zu", k);
+      }
+    }
+  }
   c->cur = 0;
   cudaError_t e = c->ops->init(c->model, f, f + n, f + (size_t)(c->D + 1) * n, c->state[0].p, c->g,
                                c->stream);

@@ -233,7 +233,16 @@ def test_errors_are_reported_before_launch(lbm):
     n0 = lbm.lbm_launch_count(lat.ctx)
     lat.init(rho, np.zeros((3, 8, 8, 8)), rho * lat.info["T0"])
     lat.step(4)
-    assert lbm.lbm_launch_count(lat.ctx) == n0 + 5
+    # the check of the host fields, the equilibrium, four steps
+    assert lbm.lbm_launch_count(lat.ctx) == n0 + 6
+    # each field's first bad value is named; U must be finite
+    for bad, name in ((dict(rho=np.nan), "rho[5]"), (dict(T=0.0), "T[5]"), (dict(U=np.inf), "U")):
+        r, U, T = rho.copy(), np.zeros((3, 8, 8, 8)), rho * lat.info["T0"]
+        arr = {"rho": r, "U": U[1], "T": T}[list(bad)[0]]
+        arr.reshape(-1)[5] = list(bad.values())[0]
+        with pytest.raises(lbm.LbmError) as ei:
+            lat.init(r, U, T)
+        assert ei.value.code == lbm.LBM_EINVAL and name in str(ei.value)
 
 
 def test_grid_and_argument_limits(lbm):
