@@ -41,6 +41,28 @@ struct EqGrad {
 };
 
 
+// Pairs [first, end) of symmetry group g (g >= 1) in storage order.
+template <int M>
+struct ShellPairs {
+  static constexpr int first(int g) {
+    int p = 0;
+    while (p < Model<M>::NP && Model<M>::vs.grp[1 + 2 * p] != g) ++p;
+    return p;
+  }
+  static constexpr int end(int g) {
+    int p = first(g);
+    while (p < Model<M>::NP && Model<M>::vs.grp[1 + 2 * p] == g) ++p;
+    return p;
+  }
+};
+
+// Passes 2 and 3 as loops over each shell's pairs (lattice vectors read from
+// constant memory) instead of fully unrolled over all pairs: a smaller kernel for
+// the instruction cache.  Needs lambda in shared memory or uniform (FP32 adjoint).
+#ifndef LBM_ADJ_SHELL_LOOP
+#define LBM_ADJ_SHELL_LOOP 1
+#endif
+
 __device__ __forceinline__ double block_sum_128(double v, double* sh) {
   v = warp_sum(v);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -201,6 +223,41 @@ __global__ void __launch_bounds__(kAdjThreads, AdjMinBlocks<S>::value)
     // the vector term keeps one v = ld (A1 + s^2/2) + ls s (2 A2 + s^2/6) per pair.
     Rt m0 = Rt(0), m2 = Rt(0), m4 = Rt(0), n1 = Rt(0), n3 = Rt(0);
     Rt gvx = Rt(0), gvy = Rt(0), gvz = Rt(0);
+    constexpr bool kLoop = LBM_ADJ_SHELL_LOOP && (kSm || kFirst);
+    if constexpr (kLoop) {
+      sfor<1, Mo::G>([&](auto Gi) {
+        constexpr int gg = decltype(Gi)::value;
+        const Rt x2 = gX2<Rt>(mc, gg);
+        const Rt A1 = cf.A1(x2), A2 = cf.A2(x2);
+        m0 = m2 = m4 = n1 = n3 = gvx = gvy = gvz = Rt(0);
+#pragma unroll 1
+        for (int p = ShellPairs<M>::first(gg); p < ShellPairs<M>::end(gg); ++p) {
+          const int ip = 1 + 2 * p, im = 2 + 2 * p;
+          const Rt ex = mc.ef[ip][0], ey = mc.ef[ip][1], ez = mc.ef[ip][2];
+          const Rt s = ex * uax + ey * uay + ez * uaz;
+          const Rt s2 = s * s;
+          const Rt lp = lam(ip), lm = lam(im);
+          const Rt ls = lp + lm, ld = lp - lm;
+          const Rt tl = ls * s2, tu = ld * s;
+          m0 += ls;
+          m2 += tl;
+          m4 += tl * s2;
+          n1 += tu;
+          n3 += tu * s2;
+          const Rt v = ld * (A1 + s2 * Rt(0.5)) + (ls * s) * (Rt(2) * A2 + s2 * Rt(1.0 / 6.0));
+          gvx += ex * v;
+          gvy += ey * v;
+          gvz += ez * v;
+        }
+        const Rt w = gW<Rt>(mc, gg);
+        Lr += w * (cf.A0(x2) * m0 + A2 * m2 + m4 * Rt(1.0 / 24.0) + A1 * n1 + n3 * Rt(1.0 / 6.0));
+        Sq += w * (gr.Bq(x2) * m0 - m2 * Rt(0.25) - n1 * Rt(0.5));
+        St += w * (gr.Bt(x2) * m0 + EqGrad<Rt, D>::Dt(x2) * m2 + EqGrad<Rt, D>::Ct(x2) * n1);
+        Vx += w * gvx;
+        Vy += w * gvy;
+        Vz += w * gvz;
+      });
+    } else
     sfor<0, NP>([&](auto P) {
       constexpr int p = decltype(P)::value;
       constexpr int ip = 1 + 2 * p, im = 2 + 2 * p;
@@ -257,6 +314,19 @@ __global__ void __launch_bounds__(kAdjThreads, AdjMinBlocks<S>::value)
     const Rt oa = om * alpha, og = om * gam;
     const Rt obx = om * a_r * bx, oby = om * a_r * by, obz = om * a_r * bz;
     nu_out[self] = om1 * lam(0) + oa;
+    if constexpr (kLoop) {
+      sfor<1, Mo::G>([&](auto Gi) {
+        constexpr int gg = decltype(Gi)::value;
+        const Rt ev = oa + og * gX2<Rt>(mc, gg);
+#pragma unroll 1
+        for (int p = ShellPairs<M>::first(gg); p < ShellPairs<M>::end(gg); ++p) {
+          const int ip = 1 + 2 * p, im = 2 + 2 * p;
+          const Rt od = mc.ef[ip][0] * obx + mc.ef[ip][1] * oby + mc.ef[ip][2] * obz;
+          nu_out[(size_t)ip * g.ncell + self] = om1 * lam(ip) + (ev + od);
+          nu_out[(size_t)im * g.ncell + self] = om1 * lam(im) + (ev - od);
+        }
+      });
+    } else
     sfor<0, NP>([&](auto P) {
       constexpr int p = decltype(P)::value;
       constexpr int ip = 1 + 2 * p, im = 2 + 2 * p;

@@ -23,6 +23,7 @@ struct ModelConst {
   double T0;           // 1 / (2 c^2), lattice units
   float T0f, iT0f;     // T0 and 1 / T0 rounded to FP32
   int e[kMaxQc][3];    // lattice vectors in storage order (zero-padded to 3 components)
+  float ef[kMaxQc][3]; // the same as FP32 (loops that index directions at run time)
 };
 
 struct Grid {

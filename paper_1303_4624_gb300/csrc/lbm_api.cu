@@ -205,7 +205,10 @@ bool build_host_model(int model, HostModel* hm) {
   }
   for (int i = 0; i < vs.Q; ++i) {
     mc.w[i] = hm->w[i];
-    for (int d = 0; d < 3; ++d) mc.e[i][d] = vs.e[i][d];
+    for (int d = 0; d < 3; ++d) {
+      mc.e[i][d] = vs.e[i][d];
+      mc.ef[i][d] = (float)vs.e[i][d];
+    }
   }
   mc.a = a;
   mc.af = (float)a;
