@@ -151,6 +151,18 @@ cudaError_t step_pair_m(const void* src, void* dst, const Grid& g, double omega,
                             static_cast<S*>(dst), g, omega);
 }
 
+// The direct kernel for this grid: 32-bit element indices (where the form uses
+// them) when Q ncell fits them.
+using DirectFn = void (*)(const S*, S*, Grid, double);
+template <int M>
+DirectFn direct_kernel(const Grid& g, int rev) {
+  if constexpr (DirectNarrow<M, S>::value) {
+    if ((unsigned long long)Model<M>::Q * (unsigned long long)g.ncell <= 0xFFFFFFFFull)
+      return rev ? k_stream_collide<M, S, true, true> : k_stream_collide<M, S, false, true>;
+  }
+  return rev ? k_stream_collide<M, S, true, false> : k_stream_collide<M, S, false, false>;
+}
+
 template <int M>
 cudaError_t step_m(const void* src, void* dst, const Grid& g, double omega, int variant, int* status,
                    const StepTest* test, cudaStream_t st) {
@@ -182,20 +194,13 @@ cudaError_t step_m(const void* src, void* dst, const Grid& g, double omega, int 
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (rev)
-    return cudaLaunchKernelEx(&cfg, k_stream_collide<M, S, true>, static_cast<const S*>(src),
-                              static_cast<S*>(dst), g, omega);
-  return cudaLaunchKernelEx(&cfg, k_stream_collide<M, S, false>, static_cast<const S*>(src),
+  return cudaLaunchKernelEx(&cfg, direct_kernel<M>(g, rev), static_cast<const S*>(src),
                             static_cast<S*>(dst), g, omega);
 #else
-  if (rev)
-    k_stream_collide<M, S, true><<<grid, bx, 0, st>>>(static_cast<const S*>(src),
-                                                      static_cast<S*>(dst), g, omega);
-  else
-    k_stream_collide<M, S, false><<<grid, bx, 0, st>>>(static_cast<const S*>(src),
-                                                       static_cast<S*>(dst), g, omega);
-#endif
+  direct_kernel<M>(g, rev)<<<grid, bx, 0, st>>>(static_cast<const S*>(src), static_cast<S*>(dst), g,
+                                                omega);
   return cudaGetLastError();
+#endif
 }
 
 template <int M>

@@ -1,7 +1,8 @@
 """The full-size workloads in the benchmark's launch configuration, checked where the
 oracle can follow them.
 
-* 512 x 256 x 256 precision sweep (FP32, FP16, BF16) and the 768 x 384 x 384 FP16
+* 512 x 256 x 256 precision sweep (FP32, FP16, BF16), the same setup on 768 x 256 x
+  256 in FP32 (too large for 32-bit element indices) and the 768 x 384 x 384 FP16
   oblique Riemann problem: after the state has developed under CUDA-graph replays,
   one more step is checked cell by cell on a seeded sample (random cells, the
   corners of the box and the planes next to the diaphragm and the periodic seam):
@@ -85,6 +86,15 @@ def test_precision_sweep_512x256x256_sampled_step(lbm, storage):
     wl, fields = W.d3q95_sweep(storage=storage)
     err = check_sampled_step(lbm, wl, fields, storage, warm=64)
     assert err <= TOL[storage], err
+
+
+def test_fp32_wide_index_768x256x256_sampled_step(lbm):
+    """Q ncell = 4.78e9 exceeds 32 bits: the FP32 direct kernel forms its element
+    indices in 64 bits here (every smaller FP32 D3Q95 grid takes the 32-bit form)."""
+    wl, fields = W.d3q95_sweep(768, 256, 256, storage="fp32")
+    assert 95 * wl.cells > 2 ** 32
+    err = check_sampled_step(lbm, wl, fields, "fp32", warm=8)
+    assert err <= TOL["fp32"], err
 
 
 def test_oblique_768x384x384_fp16_sampled_step(lbm):
