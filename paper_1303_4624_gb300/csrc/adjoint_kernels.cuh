@@ -75,7 +75,7 @@ __device__ __forceinline__ double block_sum_128(double v, double* sh) {
 }
 
 #ifndef LBM_ADJ_MINB
-#define LBM_ADJ_MINB 3
+#define LBM_ADJ_MINB 4
 #endif
 #ifndef LBM_ADJ_LAM_SMEM
 #define LBM_ADJ_LAM_SMEM 1
@@ -97,7 +97,15 @@ template <int M, class L>
 constexpr int adj_smem_bytes() {
   return AdjLamSmem<L>::value ? Model<M>::Q * kAdjThreads * (int)sizeof(L) : 0;
 }
-template <int M, class S, class L, bool kFirst>
+// Address of population i at a cell: the element index in 32 bits when every index
+// of a state copy fits them (NARROW), which saves the per-population 64-bit offset
+// arithmetic; else the population's array first, then the cell.  (A macro: passed
+// through a helper function, the 64-bit form compiled to a different register
+// allocation, 168 registers with spills against 128 without.)
+#define LBM_POP(base, i, cell)                                                                \
+  (NARROW ? (base) + (uint32_t)((uint32_t)(i) * (uint32_t)g.ncell + (uint32_t)(cell))         \
+          : (base) + (size_t)(i) * g.ncell + (cell))
+template <int M, class S, class L, bool kFirst, bool NARROW>
 __global__ void __launch_bounds__(kAdjThreads, AdjMinBlocks<S>::value)
     k_adjoint(const S* __restrict__ state, const L* __restrict__ nu_next,
               const double* __restrict__ dldrho, L* __restrict__ nu_out,
@@ -142,8 +150,8 @@ __global__ void __launch_bounds__(kAdjThreads, AdjMinBlocks<S>::value)
         constexpr int ex = Mo::vs.e[ip][0], ey = Mo::vs.e[ip][1], ez = Mo::vs.e[ip][2];
         const int cm = zo[ez + RR] + yo[ey + RR] + xo[ex + RR];   // x - e_ip
         const int cp = zo[RR - ez] + yo[RR - ey] + xo[RR - ex];   // x + e_ip
-        cp_async4(dst + ip * kAdjThreads, nu_next + (size_t)ip * g.ncell + cp);
-        cp_async4(dst + im * kAdjThreads, nu_next + (size_t)im * g.ncell + cm);
+        cp_async4(dst + ip * kAdjThreads, LBM_POP(nu_next, ip, cp));
+        cp_async4(dst + im * kAdjThreads, LBM_POP(nu_next, im, cm));
       });
       cp_async_wait_all();
     }
@@ -167,11 +175,11 @@ __global__ void __launch_bounds__(kAdjThreads, AdjMinBlocks<S>::value)
       constexpr bool last = (p + 1 == NP) || (Mo::vs.grp[ip + 2] != gg);
       const int cm = zo[ez + RR] + yo[ey + RR] + xo[ex + RR];   // x - e_ip
       const int cp = zo[RR - ez] + yo[RR - ey] + xo[RR - ex];   // x + e_ip
-      const Rt hp = (Rt)Codec<S>::ld(state + (size_t)ip * g.ncell + cm);
-      const Rt hm = (Rt)Codec<S>::ld(state + (size_t)im * g.ncell + cp);
+      const Rt hp = (Rt)Codec<S>::ld(LBM_POP(state, ip, cm));
+      const Rt hm = (Rt)Codec<S>::ld(LBM_POP(state, im, cp));
       if constexpr (!kSm && !kFirst) {
-        lam_r[ip] = nu_next[(size_t)ip * g.ncell + cp];
-        lam_r[im] = nu_next[(size_t)im * g.ncell + cm];
+        lam_r[ip] = *LBM_POP(nu_next, ip, cp);
+        lam_r[im] = *LBM_POP(nu_next, im, cm);
       }
       if constexpr (first) gs = gjx = gjy = gjz = gsg = Rt(0);
       const Rt sp = hp + hm, dm = hp - hm;
@@ -322,8 +330,8 @@ __global__ void __launch_bounds__(kAdjThreads, AdjMinBlocks<S>::value)
         for (int p = ShellPairs<M>::first(gg); p < ShellPairs<M>::end(gg); ++p) {
           const int ip = 1 + 2 * p, im = 2 + 2 * p;
           const Rt od = mc.ef[ip][0] * obx + mc.ef[ip][1] * oby + mc.ef[ip][2] * obz;
-          nu_out[(size_t)ip * g.ncell + self] = om1 * lam(ip) + (ev + od);
-          nu_out[(size_t)im * g.ncell + self] = om1 * lam(im) + (ev - od);
+          *LBM_POP(nu_out, ip, self) = om1 * lam(ip) + (ev + od);
+          *LBM_POP(nu_out, im, self) = om1 * lam(im) + (ev - od);
         }
       });
     } else
@@ -337,8 +345,8 @@ __global__ void __launch_bounds__(kAdjThreads, AdjMinBlocks<S>::value)
       if constexpr (ex != 0) od += Rt(ex) * obx;
       if constexpr (ey != 0) od += Rt(ey) * oby;
       if constexpr (ez != 0) od += Rt(ez) * obz;
-      nu_out[(size_t)ip * g.ncell + self] = om1 * lam(ip) + (ev + od);
-      nu_out[(size_t)im * g.ncell + self] = om1 * lam(im) + (ev - od);
+      *LBM_POP(nu_out, ip, self) = om1 * lam(ip) + (ev + od);
+      *LBM_POP(nu_out, im, self) = om1 * lam(im) + (ev - od);
     });
   }
   const double bsum = block_sum_128(om_part, sh);
@@ -347,6 +355,8 @@ __global__ void __launch_bounds__(kAdjThreads, AdjMinBlocks<S>::value)
     omega_acc[b] += bsum;
   }
 }
+
+#undef LBM_POP
 
 // dL/d(rho0, U0, T0): lambda_0(x, i) = nu0(x + e_i, i) contracted with the
 // derivatives of f_i^eq(rho, u, theta) at the initial fields (FP64).

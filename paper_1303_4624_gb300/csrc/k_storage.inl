@@ -225,12 +225,25 @@ cudaError_t set_f_m(const double* f, void* dst, const Grid& g, cudaStream_t st) 
 
 using L = std::conditional<std::is_same<S, double>::value, double, float>::type;
 
+// The adjoint kernel for this grid: 32-bit element indices (FP32 adjoint) when
+// Q ncell fits them.
+using AdjointFn = void (*)(const S*, const L*, const double*, L*, double*, Grid, double);
+template <int M, bool kFirst>
+AdjointFn adjoint_kernel(const Grid& g) {
+  if constexpr (std::is_same<L, float>::value) {
+    if ((unsigned long long)Model<M>::Q * (unsigned long long)g.ncell <= 0xFFFFFFFFull)
+      return k_adjoint<M, S, L, kFirst, true>;
+  }
+  return k_adjoint<M, S, L, kFirst, false>;
+}
+
 template <int M>
 cudaError_t adjoint_m(const void* state_n, const void* nu_next, const double* dldrho, void* nu_out,
                       double* omega_acc, const Grid& g, double omega, cudaStream_t st) {
   const int bx = cell_block_x(g.nx);
   const dim3 grid((unsigned)((g.nx + bx - 1) / bx), (unsigned)g.ny, (unsigned)g.nz);
   constexpr int smem = adj_smem_bytes<M, L>();
+  const AdjointFn kern = dldrho ? adjoint_kernel<M, true>(g) : adjoint_kernel<M, false>(g);
   if constexpr (smem > 0) {
     // Dynamic shared memory above the 48 KB default needs the opt-in, once per device.
     static std::mutex mu;
@@ -240,11 +253,10 @@ cudaError_t adjoint_m(const void* state_n, const void* nu_next, const double* dl
     if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lk(mu);
     if (done_dev[dev & 15] != dev) {
-      e = cudaFuncSetAttribute(k_adjoint<M, S, L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               smem);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_adjoint<M, S, L, false>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      const AdjointFn all[4] = {k_adjoint<M, S, L, true, false>, k_adjoint<M, S, L, false, false>,
+                                k_adjoint<M, S, L, true, true>, k_adjoint<M, S, L, false, true>};
+      for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+        e = cudaFuncSetAttribute(all[k], cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
       if (e != cudaSuccess) return e;
       done_dev[dev & 15] = dev;
     }
@@ -260,10 +272,10 @@ cudaError_t adjoint_m(const void* state_n, const void* nu_next, const double* dl
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   if (dldrho)
-    return cudaLaunchKernelEx(&cfg, k_adjoint<M, S, L, true>, static_cast<const S*>(state_n),
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<const S*>(state_n),
                               static_cast<const L*>(nullptr), dldrho, static_cast<L*>(nu_out),
                               omega_acc, g, omega);
-  return cudaLaunchKernelEx(&cfg, k_adjoint<M, S, L, false>, static_cast<const S*>(state_n),
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<const S*>(state_n),
                             static_cast<const L*>(nu_next), static_cast<const double*>(nullptr),
                             static_cast<L*>(nu_out), omega_acc, g, omega);
 }
