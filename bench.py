@@ -353,7 +353,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def e2e_leg(lbm, W, wl, fields, steps, stream):
+def e2e_leg(lbm, W, wl, fields, steps, stream, reps=3):
     """Whole job through the public API from pinned host buffers: lbm_init from
     host fields, `steps` steps, lbm_moments back to host; timed on the host clock."""
     import numpy as np
@@ -370,17 +370,22 @@ def e2e_leg(lbm, W, wl, fields, steps, stream):
     lat.init(rho, U, T)   # warm-up of the path
     lbm.lbm_moments(lat.ctx, out_r, out_U, out_T)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    lat.init(rho, U, T)
-    lat.step(steps)
-    lbm.lbm_moments(lat.ctx, out_r, out_U, out_T)
-    dt = time.perf_counter() - t0
+    runs = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        lat.init(rho, U, T)
+        lat.step(steps)
+        lbm.lbm_moments(lat.ctx, out_r, out_U, out_T)
+        runs.append(time.perf_counter() - t0)
     lat.close()
+    dt = sorted(runs)[len(runs) // 2]
     h2d = rho.nbytes + U.nbytes + T.nbytes
     d2h = out_r.nbytes + out_U.nbytes + out_T.nbytes
     return {"value": round(wl.cells * steps / dt / 1e6, 1), "unit": "MLUPS",
             "h2d_bytes_per_step": round(h2d / steps, 1), "d2h_bytes_per_step": round(d2h / steps, 1),
-            "note": "one lbm_init from host fields + %d steps + lbm_moments to host, host clock" % steps}
+            "runs_ms": [round(r * 1e3, 2) for r in runs],
+            "note": "one lbm_init from host fields + %d steps + lbm_moments to host, host clock; "
+                    "median of %d runs" % (steps, reps)}
 
 
 def moments_leg(lbm, W, stream, lat=None, wl=None, calls=200):

@@ -144,11 +144,12 @@ cudaError_t step_pair_m(const void* src, void* dst, const Grid& g, double omega,
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (rev)
-    return cudaLaunchKernelEx(&cfg, k_stream_collide_pair<M, S, true>, static_cast<const S*>(src),
-                              static_cast<S*>(dst), g, omega);
-  return cudaLaunchKernelEx(&cfg, k_stream_collide_pair<M, S, false>, static_cast<const S*>(src),
-                            static_cast<S*>(dst), g, omega);
+  auto kern = rev ? k_stream_collide_pair<M, S, true, false> : k_stream_collide_pair<M, S, false, false>;
+  if constexpr (PairNarrow<M>::value) {
+    if ((unsigned long long)Model<M>::Q * (unsigned long long)g.ncell <= 0xFFFFFFFFull)
+      kern = rev ? k_stream_collide_pair<M, S, true, true> : k_stream_collide_pair<M, S, false, true>;
+  }
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<const S*>(src), static_cast<S*>(dst), g, omega);
 }
 
 // The direct kernel for this grid: 32-bit element indices (where the form uses

@@ -77,17 +77,25 @@ template <int M>
 struct PairMinBlocks {
   static constexpr int value = M == 1 ? LBM_PAIR_MINB_D3Q95 : LBM_PAIR_MINB_D2Q33;
 };
+// 32-bit element indices (see k_stream_collide's NARROW) for D3Q95 when Q ncell fits
+// them: 11.9 against 11.4 GLUPS in FP16 at 512x256x256; D2Q33 measured slower with
+// them (37.6 against 38.3 GLUPS at 4096x2048).
+template <int M>
+struct PairNarrow {
+  static constexpr bool value = M == 1;
+};
 
 // The Q packed pairs stay in registers between the gather and their two uses.
 // D3Q95 (CHAIN): the relaxation decodes direction i's pair only once the previous
 // direction's result exists (the packed pair is OR-ed with that result masked by a
-// zero read from constant memory, which the compiler cannot see through).
-// Without the dependency the compiler decodes all 95 pairs ahead of their use:
-// 190 more live registers, so the kernel needed 255 registers (8 warps per SM)
-// and still spilled; with it, 168 (12 warps per SM).  One extra integer
-// instruction per direction; the values, and so the results, are unchanged.
+// zero read from constant memory, which the compiler cannot see through).  Without
+// the dependency the compiler decodes the pairs ahead of their use: 190 more live
+// registers, so the kernel needed 255 registers (8 warps per SM) and still spilled;
+// with it, 168 (12 warps per SM).  One extra integer instruction per direction; the
+// values, and so the results, are unchanged.  D2Q33 fits without it, and measured
+// slower with it (36.8-37.8 against 38.3 GLUPS at 4096x2048).
 // REV: walk the blocks in reverse order (see k_stream_collide).
-template <int M, class S, bool REV>
+template <int M, class S, bool REV, bool NARROW>
 __global__ void __launch_bounds__(kPairThreads, PairMinBlocks<M>::value)
     k_stream_collide_pair(const S* __restrict__ src, S* __restrict__ dst, Grid g, double omega) {
   using Mo = Model<M>;
@@ -111,13 +119,23 @@ __global__ void __launch_bounds__(kPairThreads, PairMinBlocks<M>::value)
   sfor<0, Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
     constexpr int ex = Mo::vs.e[i][0], ey = Mo::vs.e[i][1], ez = Mo::vs.e[i][2];
-    const S* row = src + (size_t)i * (size_t)g.ncell + (zo[ez + RR] + yo[ey + RR]);
     const int xs = xo[ex + RR];                    // (x - e_x) mod Nx
-    if constexpr ((ex & 1) == 0) {
-      h2[i] = __ldg(reinterpret_cast<const P*>(row + xs));   // xs even: aligned pair
+    if constexpr (NARROW) {
+      const uint32_t row = (uint32_t)i * (uint32_t)g.ncell + (uint32_t)(zo[ez + RR] + yo[ey + RR]);
+      if constexpr ((ex & 1) == 0) {
+        h2[i] = __ldg(reinterpret_cast<const P*>(src + (row + (uint32_t)xs)));
+      } else {
+        const int xs1 = (xs + 1 == g.nx) ? 0 : xs + 1;     // (x + 1 - e_x) mod Nx
+        h2[i] = PC::make(__ldg(src + (row + (uint32_t)xs)), __ldg(src + (row + (uint32_t)xs1)));
+      }
     } else {
-      const int xs1 = (xs + 1 == g.nx) ? 0 : xs + 1;       // (x + 1 - e_x) mod Nx
-      h2[i] = PC::make(__ldg(row + xs), __ldg(row + xs1));
+      const S* row = src + (size_t)i * (size_t)g.ncell + (zo[ez + RR] + yo[ey + RR]);
+      if constexpr ((ex & 1) == 0) {
+        h2[i] = __ldg(reinterpret_cast<const P*>(row + xs));   // xs even: aligned pair
+      } else {
+        const int xs1 = (xs + 1 == g.nx) ? 0 : xs + 1;     // (x + 1 - e_x) mod Nx
+        h2[i] = PC::make(__ldg(row + xs), __ldg(row + xs1));
+      }
     }
   });
   S* const obase = dst + (((size_t)z * g.ny + y) * g.nx + x);
@@ -136,9 +154,14 @@ __global__ void __launch_bounds__(kPairThreads, PairMinBlocks<M>::value)
       },
       omega,
       [&](auto I, float2 v) {
+        constexpr int i = decltype(I)::value;
         const P pv = PC::enc(v);
         if constexpr (CHAIN) last = *reinterpret_cast<const uint32_t*>(&pv);
-        *reinterpret_cast<P*>(obase + (size_t)decltype(I)::value * (size_t)g.ncell) = pv;
+        if constexpr (NARROW)
+          *reinterpret_cast<P*>(dst + ((uint32_t)i * (uint32_t)g.ncell +
+                                       (uint32_t)((z * g.ny + y) * g.nx + x))) = pv;
+        else
+          *reinterpret_cast<P*>(obase + (size_t)i * (size_t)g.ncell) = pv;
       });
 }
 

@@ -3,7 +3,7 @@ oracle can follow them.
 
 * 512 x 256 x 256 precision sweep (FP32, FP16, BF16), the same setup on 768 x 256 x
   256 in FP32 (too large for 32-bit element indices) and the 768 x 384 x 384 FP16
-  oblique Riemann problem: after the state has developed under CUDA-graph replays,
+  oblique Riemann problem (default kernel and the two-cell kernel): after the state has developed under CUDA-graph replays,
   one more step is checked cell by cell on a seeded sample (random cells, the
   corners of the box and the planes next to the diaphragm and the periodic seam):
   the oracle collides the populations the GPU gathered (its stored state, decoded
@@ -44,13 +44,15 @@ def sample_cells(dims, n, seed):
     return np.array(xs), np.array(ys), np.array(zs)
 
 
-def check_sampled_step(lbm, wl, fields, storage, warm, nsample=4000, seed=3):
+def check_sampled_step(lbm, wl, fields, storage, warm, nsample=4000, seed=3, variant=None):
     import torch
     mdl = get_model("D3Q95")
     Q = mdl.Q
     nx, ny, nz = wl.dims
     lat = lbm.Lattice("D3Q95", wl.dims, wl.omega, storage)
     lbm.lbm_set_graph_steps(lat.ctx, 32)
+    if variant is not None:
+        lbm.lbm_set_variant(lat.ctx, variant)
     lat.init(fields.rho, fields.U, fields.theta * lat.info["T0"])
     lat.step(warm)
     dt = getattr(torch, TORCH_DTYPE[storage])
@@ -97,9 +99,13 @@ def test_fp32_wide_index_768x256x256_sampled_step(lbm):
     assert err <= TOL["fp32"], err
 
 
-def test_oblique_768x384x384_fp16_sampled_step(lbm):
+@pytest.mark.parametrize("variant", ["auto", "pair"])
+def test_oblique_768x384x384_fp16_sampled_step(lbm, variant):
+    """variant "pair": the two-cell kernel with 64-bit element indices (Q ncell =
+    1.08e10 exceeds 32 bits)."""
     wl, fields = W.d3q95_oblique()
-    err = check_sampled_step(lbm, wl, fields, "fp16", warm=32)
+    v = None if variant == "auto" else lbm.VARIANT_PAIR
+    err = check_sampled_step(lbm, wl, fields, "fp16", warm=32, variant=v)
     assert err <= TOL["fp16"], err
 
 
