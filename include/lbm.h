@@ -183,11 +183,14 @@ int lbm_set_stream(lbm_ctx* ctx, void* stream);
  * defined after the Maxwellian.
  *   rho [cells], U [D][cells] (lattice units), T [cells] (lattice units),
  *   all FP64 in `where` memory.  rho > 0 and T > 0 and all values finite:
- *   for LBM_HOST inputs this is checked on the device right after the upload
- *   (one pass at HBM speed, then one blocking read of the result), before the
- *   equilibrium is launched; a refused call leaves the populations as they were
- *   but invalidates a recorded rollout.  LBM_DEVICE inputs are not inspected
- *   (the call stays asynchronous).  The fields are also kept on the device as the
+ *   LBM_HOST inputs are uploaded in chunks (large grids: 8) on a stream of the
+ *   context's own, each chunk checked on the device and turned into its
+ *   equilibrium while the next one uploads (pinned host memory lets the copies
+ *   overlap); the equilibrium is written to the population buffer that does not
+ *   hold the live state, which it replaces only when every value has passed the
+ *   check (one blocking read of the check's result).  A refused call leaves the
+ *   populations as they were but invalidates a recorded rollout.  LBM_DEVICE
+ *   inputs are not inspected (the call stays asynchronous).  The fields are also kept on the device as the
  *   initial state of the differentiable rollout (lbm_record / lbm_backward).
  * Errors: LBM_EINVAL, LBM_ECUDA.
  */
@@ -212,7 +215,10 @@ int64_t lbm_steps_done(const lbm_ctx* ctx);
  *   sums of the deviations (rho - 1 and E - D rho compensated, as double-float),
  *   fields formed in FP32 (relative error ~1e-7 of the stored state's exact
  *   fields).  Outputs rho [cells], U [D][cells], T [cells] as FP64 in `where`
- *   memory; any output may be NULL.
+ *   memory; any output may be NULL.  LBM_DEVICE: enqueued on the context's
+ *   stream.  LBM_HOST: computed in chunks (large grids: 8), each read back on the
+ *   context's copy stream while the next is computed; returns once the host
+ *   arrays are filled (pinned host memory lets the copies overlap).
  * Errors: LBM_ESTATE, LBM_EINVAL, LBM_ECUDA.
  */
 int lbm_moments(lbm_ctx* ctx, double* rho, double* U, double* T, int where);

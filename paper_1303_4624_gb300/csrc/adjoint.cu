@@ -166,7 +166,8 @@ int lbm_record(lbm_ctx* ctx, int64_t nsteps, int64_t ckpt_every) {
   }
   const double* f = static_cast<const double*>(v.fields->p);
   const size_t n = (size_t)v.g.ncell;
-  cudaError_t e = v.ops->init(v.model, f, f + n, f + (size_t)(v.D + 1) * n, r.ckpt[0]->p, v.g, v.stream);
+  cudaError_t e = v.ops->init(v.model, f, f + n, f + (size_t)(v.D + 1) * n, r.ckpt[0]->p, v.g, 0,
+                                 v.g.ncell, v.stream);
   if (e != cudaSuccess) return ctx_cuda_fail(e, "init launch");
   *v.launches += 1;
   void* cur = r.ckpt[0]->p;
@@ -215,7 +216,8 @@ int lbm_record_bounded(lbm_ctx* ctx, int64_t nsteps, int64_t max_states) {
   if (rc) return rc;
   const double* f = static_cast<const double*>(v.fields->p);
   const size_t n = (size_t)v.g.ncell;
-  cudaError_t e = v.ops->init(v.model, f, f + n, f + (size_t)(v.D + 1) * n, r.ckpt[0]->p, v.g, v.stream);
+  cudaError_t e = v.ops->init(v.model, f, f + n, f + (size_t)(v.D + 1) * n, r.ckpt[0]->p, v.g, 0,
+                                 v.g.ncell, v.stream);
   if (e != cudaSuccess) return ctx_cuda_fail(e, "init launch");
   *v.launches += 1;
   const void* cur = r.ckpt[0]->p;

@@ -93,10 +93,10 @@ cudaError_t launch(int model, const void* h, const Grid& g, double* scratch, dou
   const int nb = moment_blocks(g.ncell);
   if (model == 0)
     k_moments<0, S><<<nb, kMomentThreads, 0, st>>>(static_cast<const S*>(h), g, nullptr, nullptr,
-                                                   nullptr, scratch);
+                                                   nullptr, scratch, 0, g.ncell);
   else
     k_moments<1, S><<<nb, kMomentThreads, 0, st>>>(static_cast<const S*>(h), g, nullptr, nullptr,
-                                                   nullptr, scratch);
+                                                   nullptr, scratch, 0, g.ncell);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_audit_reduce<<<1, 256, 0, st>>>(scratch, nb, out);

@@ -16,12 +16,14 @@ struct ModelConst {
   double X2[kMaxGc];   // |xi|^2 = a^2 |e|^2 of each group
   float Wf[kMaxGc];
   float X2f[kMaxGc];
+  float X2lo[kMaxGc];  // X2 - X2f: with X2f, X2 as a double-float (hi, lo) pair
   double w[kMaxQc];    // weight per direction (storage order)
   double a;            // sqrt(2) c: xi_i = a e_i
-  float af;
+  float af, alo;       // a rounded to FP32, and a - af
   double c;
   double T0;           // 1 / (2 c^2), lattice units
   float T0f, iT0f;     // T0 and 1 / T0 rounded to FP32
+  float iT0lo;         // 1 / T0 - iT0f
   int e[kMaxQc][3];    // lattice vectors in storage order (zero-padded to 3 components)
   float ef[kMaxQc][3]; // the same as FP32 (loops that index directions at run time)
 };
@@ -43,8 +45,9 @@ struct StepTest {
 struct StorageOps {
   int elem_bytes;
   cudaError_t (*upload)(const ModelConst* mc2);
+  // The equilibrium of the fields for cells [begin, end) (U strided by g.ncell).
   cudaError_t (*init)(int model, const double* rho, const double* U, const double* T, void* dst,
-                      const Grid& g, cudaStream_t st);
+                      const Grid& g, long long begin, long long end, cudaStream_t st);
   // One stream-collide step.  variant: kVariantDirect, kVariantTma, kVariantSplit or
   // kVariantPair, or-ed with kStepReverse for the direct and pair kernels (the caller
   // checks applicability: Nx % 8 == 0 for TMA, Nx even and 16-bit storage for pair).  status: device int
@@ -55,8 +58,11 @@ struct StorageOps {
   // One-time per-device launch set-up of the TMA kernels (shared-memory opt-in and
   // occupancy), done before any stream capture.
   cudaError_t (*prepare_tma)(int model);
+  // Moments and audit partials of blocks [block0, block0 + nblocks) of kMomentThreads
+  // cells (moment_blocks(ncell) blocks cover the grid).
   cudaError_t (*moments)(int model, const void* src, const Grid& g, double* rho, double* U,
-                         double* T, double* partials, cudaStream_t st);
+                         double* T, double* partials, long long block0, long long nblocks,
+                         cudaStream_t st);
   cudaError_t (*get_f)(int model, const void* src, double* f, const Grid& g, cudaStream_t st);
   cudaError_t (*set_f)(int model, const double* f, void* dst, const Grid& g, cudaStream_t st);
   // Overwrite the first / last `width` planes along `axis` (0 x, 1 y, 2 z) with the
@@ -87,10 +93,12 @@ inline long long cell_blocks(const Grid& g) {
   return (long long)((g.nx + bx - 1) / bx) * g.ny * g.nz;
 }
 cudaError_t launch_sum_reduce(const double* partials, long long n, double* out, cudaStream_t st);
-// *first_bad = min over bad values of (index << 2 | field) (0 rho, 1 U, 2 T); the
-// caller presets it to all ones.
+// Cells [begin, end) of fields with n cells (U strided by n): *first_bad = min over
+// bad values of (index << 2 | field) (0 rho, 1 U, 2 T); the caller presets it to all
+// ones.
 cudaError_t launch_check_fields(const double* rho, const double* U, const double* T, long long n,
-                                int D, unsigned long long* first_bad, cudaStream_t st);
+                                long long begin, long long end, int D,
+                                unsigned long long* first_bad, cudaStream_t st);
 
 extern const StorageOps kOpsFP64, kOpsFP32, kOpsFP16, kOpsBF16;
 

@@ -16,9 +16,10 @@ cudaError_t launch_audit_reduce(const double* partials, int nblocks, double* out
 // finite (NaN fails every comparison).  *first_bad (preset to all ones) receives the
 // smallest (index << 2 | field) of a bad value, field 0 rho, 1 U, 2 T.
 static __global__ void k_check_fields(const double* __restrict__ rho, const double* __restrict__ U,
-                                      const double* __restrict__ T, long long n, int D,
+                                      const double* __restrict__ T, long long n, long long begin,
+                                      long long end, int D,
                                       unsigned long long* __restrict__ first_bad) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+  for (long long i = begin + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < end;
        i += (long long)gridDim.x * blockDim.x) {
     int field = -1;
     const double r = rho[i], t = T[i];
@@ -33,9 +34,12 @@ static __global__ void k_check_fields(const double* __restrict__ rho, const doub
 }
 
 cudaError_t launch_check_fields(const double* rho, const double* U, const double* T, long long n,
-                                int D, unsigned long long* first_bad, cudaStream_t st) {
-  const long long nb = (n + 255) / 256;
-  k_check_fields<<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, st>>>(rho, U, T, n, D, first_bad);
+                                long long begin, long long end, int D,
+                                unsigned long long* first_bad, cudaStream_t st) {
+  const long long nb = (end - begin + 255) / 256;
+  if (nb <= 0) return cudaSuccess;
+  k_check_fields<<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, st>>>(rho, U, T, n, begin, end, D,
+                                                                    first_bad);
   return cudaGetLastError();
 }
 

@@ -1,6 +1,7 @@
 // k_storage.inl - launchers of one storage form.  Included by k_fp64.cu,
 // k_fp32.cu, k_fp16.cu and k_bf16.cu after defining LBM_STORE (element type) and
 // LBM_OPS (name of the StorageOps table).
+#include <algorithm>
 #include <mutex>
 
 #include "kernels.cuh"
@@ -22,10 +23,11 @@ cudaError_t upload(const ModelConst* mc2) {
 
 template <int M>
 cudaError_t init_m(const double* rho, const double* U, const double* T, void* dst, const Grid& g,
-                   cudaStream_t st) {
+                   long long begin, long long end, cudaStream_t st) {
   const int bs = 256;
-  const long long nb = (g.ncell + bs - 1) / bs;
-  k_init<M, S><<<(unsigned)nb, bs, 0, st>>>(rho, U, T, static_cast<S*>(dst), g);
+  const long long nb = (end - begin + bs - 1) / bs;
+  if (nb <= 0) return cudaSuccess;
+  k_init<M, S><<<(unsigned)nb, bs, 0, st>>>(rho, U, T, static_cast<S*>(dst), g, begin, end);
   return cudaGetLastError();
 }
 
@@ -206,9 +208,11 @@ cudaError_t step_m(const void* src, void* dst, const Grid& g, double omega, int 
 
 template <int M>
 cudaError_t moments_m(const void* src, const Grid& g, double* rho, double* U, double* T,
-                      double* partials, cudaStream_t st) {
-  k_moments<M, S><<<moment_blocks(g.ncell), kMomentThreads, 0, st>>>(static_cast<const S*>(src),
-                                                                    g, rho, U, T, partials);
+                      double* partials, long long block0, long long nblocks, cudaStream_t st) {
+  if (nblocks <= 0) return cudaSuccess;
+  const long long end = std::min(g.ncell, (block0 + nblocks) * (long long)kMomentThreads);
+  k_moments<M, S><<<(unsigned)nblocks, kMomentThreads, 0, st>>>(static_cast<const S*>(src), g, rho,
+                                                                U, T, partials, block0, end);
   return cudaGetLastError();
 }
 
@@ -244,8 +248,9 @@ cudaError_t halo_copy(void* state, void* buf, const int* segs, int nseg, long lo
 }
 
 cudaError_t init(int m, const double* rho, const double* U, const double* T, void* dst,
-                 const Grid& g, cudaStream_t st) {
-  return m == 0 ? init_m<0>(rho, U, T, dst, g, st) : init_m<1>(rho, U, T, dst, g, st);
+                 const Grid& g, long long begin, long long end, cudaStream_t st) {
+  return m == 0 ? init_m<0>(rho, U, T, dst, g, begin, end, st)
+                : init_m<1>(rho, U, T, dst, g, begin, end, st);
 }
 cudaError_t step(int m, const void* src, void* dst, const Grid& g, double omega, int variant,
                  int* status, const StepTest* test, cudaStream_t st) {
@@ -253,9 +258,9 @@ cudaError_t step(int m, const void* src, void* dst, const Grid& g, double omega,
                 : step_m<1>(src, dst, g, omega, variant, status, test, st);
 }
 cudaError_t moments(int m, const void* src, const Grid& g, double* rho, double* U, double* T,
-                    double* partials, cudaStream_t st) {
-  return m == 0 ? moments_m<0>(src, g, rho, U, T, partials, st)
-                : moments_m<1>(src, g, rho, U, T, partials, st);
+                    double* partials, long long block0, long long nblocks, cudaStream_t st) {
+  return m == 0 ? moments_m<0>(src, g, rho, U, T, partials, block0, nblocks, st)
+                : moments_m<1>(src, g, rho, U, T, partials, block0, nblocks, st);
 }
 cudaError_t get_f(int m, const void* src, double* f, const Grid& g, cudaStream_t st) {
   return m == 0 ? get_f_m<0>(src, f, g, st) : get_f_m<1>(src, f, g, st);

@@ -743,8 +743,11 @@ __global__ void __launch_bounds__(kSplitThreads, LBM_SPLIT_MINB)
 // h_i = rho P_i(u, theta) - 1 for the fields rho, U (lattice), T (lattice) of each cell,
 // rounded once to the storage type.  FP64, or (FP32 storage) double-float on the
 // FP32 pipe, whose ~48 significant bits round to the same FP32 value as FP64 except
-// within 2^-44 relative of a rounding boundary: on this GPU the FP64 form of the
-// 95 direction polynomials is bound by the FP64 pipe (~38 ms for 33.5 M cells).
+// within 2^-44 relative of a rounding boundary.  The FP32 form splits its five FP64
+// inputs into double-float once and does everything else on the FP32 pipe: on this
+// GPU the FP64 pipe issues 1/64 of the FP32 rate, and the FP64 form of the 95
+// direction polynomials is bound by it (~38 ms for 33.5 M cells; with the shell
+// coefficients alone in FP64, ~13 ms).
 
 // double-float helpers (FMA products, Knuth / Dekker sums; see ff_add)
 __device__ __forceinline__ FF ff_from(double d) {
@@ -762,18 +765,21 @@ __device__ __forceinline__ FF ff_mul(FF a, FF b) {
   e = __fmaf_rn(a.lo, b.hi, e);
   return ff_renorm(p, e);
 }
+// a times an FP32 constant c
+__device__ __forceinline__ FF ff_mulc(FF a, float c) {
+  const float p = __fmul_rn(c, a.hi);
+  float e = __fmaf_rn(c, a.hi, -p);
+  e = __fmaf_rn(c, a.lo, e);
+  return ff_renorm(p, e);
+}
 template <int K>
 __device__ __forceinline__ FF ff_scale(FF a) {
   if constexpr (K == 1) return a;
   else if constexpr (K == -1) return {-a.hi, -a.lo};
-  else {
-    const float p = __fmul_rn((float)K, a.hi);
-    float e = __fmaf_rn((float)K, a.hi, -p);
-    e = __fmaf_rn((float)K, a.lo, e);
-    return ff_renorm(p, e);
-  }
+  else return ff_mulc(a, (float)K);
 }
 __device__ __forceinline__ FF ff_neg(FF a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ FF ff_const(float c) { return {c, 0.f}; }
 
 // s = e . (a u) as double-float for a compile-time lattice vector e
 template <int EX, int EY, int EZ>
@@ -786,46 +792,68 @@ __device__ __forceinline__ FF ff_edot(FF vx, FF vy, FF vz) {
   return s;
 }
 
+// Cells [begin, end) of the grid (U and the populations strided by g.ncell).
 template <int M, class S>
 __global__ void __launch_bounds__(256)
     k_init(const double* __restrict__ rho, const double* __restrict__ U,
-           const double* __restrict__ T, S* __restrict__ dst, Grid g) {
+           const double* __restrict__ T, S* __restrict__ dst, Grid g, long long begin,
+           long long end) {
   using Mo = Model<M>;
   constexpr int D = Mo::D, NP = Mo::NP;
   const ModelConst& mc = c_mc[M];
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= g.ncell) return;
+  const long long idx = begin + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= end) return;
   if constexpr (std::is_same<S, float>::value) {
-    // per cell in FP64 (a few dozen operations), per direction in double-float
-    const double rd = rho[idx];
-    const double ux = mc.a * U[idx];
-    const double uy = mc.a * U[g.ncell + idx];
-    const double uz = (D == 3) ? mc.a * U[2 * g.ncell + idx] : 0.0;
-    const double theta = T[idx] / mc.T0;
-    const EqCoef<double, D> cf(ux * ux + uy * uy + uz * uz, theta - 1.0);
-    const FF r = ff_from(rd), m1 = {-1.f, 0.f};
-    const FF vx = ff_from(mc.a * ux), vy = ff_from(mc.a * uy), vz = ff_from(mc.a * uz);
-    const FF c24 = ff_from(1.0 / 24.0), c6 = ff_from(1.0 / 6.0);
-    dst[idx] = (float)(rd * cf.K0 - 1.0);
-    FF a0 = {0.f, 0.f}, a1 = a0, a2 = a0;
+    // the coefficients of EqCoef (see there), with rho folded in per shell:
+    //   h_i = (rho - 1) + rho (A0 - 1) + rho A2 s^2 + rho s^4 / 24 + s (rho A1 + rho s^2 / 6)
+    constexpr double kSixth = 1.0 / 6.0, kTwentyFourth = 1.0 / 24.0;
+    constexpr float c6h = (float)kSixth, c6l = (float)(kSixth - (double)c6h);
+    constexpr float c24h = (float)kTwentyFourth, c24l = (float)(kTwentyFourth - (double)c24h);
+    const FF a = {mc.af, mc.alo};
+    const FF r = ff_from(rho[idx]);
+    const FF ux = ff_mul(ff_from(U[idx]), a);
+    const FF uy = ff_mul(ff_from(U[g.ncell + idx]), a);
+    const FF uz = (D == 3) ? ff_mul(ff_from(U[2 * g.ncell + idx]), a) : FF{0.f, 0.f};
+    const FF q = ff_add(ff_add(ff_mul(ux, ux), ff_mul(uy, uy)), ff_mul(uz, uz));
+    const FF t = ff_add(ff_mul(ff_from(T[idx]), FF{mc.iT0f, mc.iT0lo}), ff_const(-1.f));
+    const FF K0m1 =
+        ff_add(ff_mul(t, ff_add(ff_add(ff_mulc(t, 0.125f * D * (D + 2)), ff_mulc(q, 0.25f * (D + 2))),
+                                ff_const(-0.5f * D))),
+               ff_mul(q, ff_add(ff_mulc(q, 0.125f), ff_const(-0.5f))));
+    const FF K1 = ff_mul(t, ff_add(ff_add(ff_mulc(t, -0.25f * (D + 2)), ff_mulc(q, -0.25f)),
+                                   ff_const(0.5f)));
+    const FF K2 = ff_mulc(ff_mul(t, t), 0.125f);
+    const FF L0 = ff_add(ff_add(ff_mulc(t, -0.5f * (D + 2)), ff_mulc(q, -0.5f)), ff_const(1.f));
+    const FF L1 = ff_mulc(t, 0.5f);
+    const FF M0 = ff_add(ff_add(ff_mulc(t, -0.25f * (D + 4)), ff_mulc(q, -0.25f)), ff_const(0.5f));
+    const FF M1 = ff_mulc(t, 0.25f);
+    const FF rm1 = ff_add(r, ff_const(-1.f));
+    const FF vx = ff_mul(ux, a), vy = ff_mul(uy, a), vz = ff_mul(uz, a);
+    const FF r6 = ff_mul(r, FF{c6h, c6l}), r24 = ff_mul(r, FF{c24h, c24l});
+    {
+      const FF h0 = ff_add(rm1, ff_mul(r, K0m1));
+      dst[idx] = __fadd_rn(h0.hi, h0.lo);   // one rounding to FP32
+    }
+    FF R0 = {0.f, 0.f}, R1 = R0, R2 = R0;
     sfor<0, NP>([&](auto P) {
       constexpr int p = decltype(P)::value;
       constexpr int ip = 1 + 2 * p, im = 2 + 2 * p;
       constexpr int gg = Mo::vs.grp[ip];
       constexpr bool first = (p == 0) || (Mo::vs.grp[ip - 2] != gg);
       constexpr int ex = Mo::vs.e[ip][0], ey = Mo::vs.e[ip][1], ez = Mo::vs.e[ip][2];
-      if constexpr (first) {   // the shell's coefficients, once per shell, from FP64
-        const double x2 = mc.X2[gg];
-        a0 = ff_from(cf.A0(x2));
-        a1 = ff_from(cf.A1(x2));
-        a2 = ff_from(cf.A2(x2));
+      if constexpr (first) {   // the shell's coefficients, once per shell
+        const FF x2 = {mc.X2f[gg], mc.X2lo[gg]};
+        const FF A0m1 = ff_add(K0m1, ff_mul(x2, ff_add(K1, ff_mul(x2, K2))));
+        R0 = ff_add(rm1, ff_mul(r, A0m1));
+        R1 = ff_mul(r, ff_add(L0, ff_mul(L1, x2)));
+        R2 = ff_mul(r, ff_add(M0, ff_mul(M1, x2)));
       }
       const FF s = ff_edot<ex, ey, ez>(vx, vy, vz);
       const FF s2 = ff_mul(s, s);
-      const FF ev = ff_add(a0, ff_mul(s2, ff_add(a2, ff_mul(s2, c24))));
-      const FF od = ff_mul(s, ff_add(a1, ff_mul(s2, c6)));
-      const FF hp = ff_add(ff_mul(r, ff_add(ev, od)), m1);
-      const FF hm = ff_add(ff_mul(r, ff_add(ev, ff_neg(od))), m1);
+      const FF ev = ff_add(R0, ff_mul(s2, ff_add(R2, ff_mul(s2, r24))));
+      const FF od = ff_mul(s, ff_add(R1, ff_mul(s2, r6)));
+      const FF hp = ff_add(ev, od);
+      const FF hm = ff_add(ev, ff_neg(od));
       dst[(size_t)ip * g.ncell + idx] = __fadd_rn(hp.hi, hp.lo);   // one rounding to FP32
       dst[(size_t)im * g.ncell + idx] = __fadd_rn(hm.hi, hm.lo);
     });
@@ -886,7 +914,8 @@ __device__ __forceinline__ double warp_min(double v) {
 // (rest-state moments: sum w = 1, sum w xi = 0, sum w |xi|^2 = D).
 template <int M, class S>
 __device__ __forceinline__ void moments_fp32_forms(const S* __restrict__ src, const Grid& g,
-                                                   long long idx, double* __restrict__ rho_out,
+                                                   long long idx, long long end, long long block,
+                                                   double* __restrict__ rho_out,
                                                    double* __restrict__ U_out,
                                                    double* __restrict__ T_out,
                                                    double* __restrict__ partials) {
@@ -896,7 +925,7 @@ __device__ __forceinline__ void moments_fp32_forms(const S* __restrict__ src, co
   const ModelConst& mc = c_mc[M];
   FF srd = {0.f, 0.f}, sed = {0.f, 0.f}, sjx = {0.f, 0.f}, sjy = {0.f, 0.f}, sjz = {0.f, 0.f};
   float hmin = 3.0e38f, bad = 0.f, cnt = 0.f;
-  if (idx < g.ncell) {
+  if (idx < end) {
     auto hv = [&](auto I) {
       const float v = Codec<S>::ld(src + (size_t)decltype(I)::value * (size_t)g.ncell + idx);
       hmin = fminf(hmin, v);
@@ -974,7 +1003,7 @@ __device__ __forceinline__ void moments_fp32_forms(const S* __restrict__ src, co
     if (k == 0) d += (double)n;                                  // mass = n + sum (rho - 1)
     if (k == 4) d = 0.5 * mc.T0 * ((double)D * (double)n + d);   // energy
     if (k == 5) d = (n > 0.f) ? 1.0 + d : 1e300;                 // min f / w over the block
-    partials[(size_t)blockIdx.x * kAuditSlots + k] = d;
+    partials[(size_t)block * kAuditSlots + k] = d;
   }
 }
 
@@ -982,20 +1011,24 @@ template <class S>
 struct MomMinBlocks {
   static constexpr int value = std::is_same<S, double>::value ? 1 : LBM_MOM_MINB;
 };
+// Blocks block0, block0 + 1, ... of kMomentThreads cells each, cells below end (the
+// audit partials of block b go to slot b, so a launch over part of the grid writes
+// the same partials as the whole-grid launch writes for those blocks).
 template <int M, class S>
 __global__ void __launch_bounds__(kMomentThreads, MomMinBlocks<S>::value)
     k_moments(const S* __restrict__ src, Grid g, double* __restrict__ rho_out,
               double* __restrict__ U_out, double* __restrict__ T_out,
-              double* __restrict__ partials) {
+              double* __restrict__ partials, long long block0, long long end) {
   using Mo = Model<M>;
   constexpr int D = Mo::D, Q = Mo::Q;
   const ModelConst& mc = c_mc[M];
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long block = block0 + blockIdx.x;
+  const long long idx = block * blockDim.x + threadIdx.x;
   double acc[kAuditSlots] = {0, 0, 0, 0, 0, 1e300, 0, 0};
   if constexpr (!std::is_same<S, double>::value) {
-    moments_fp32_forms<M, S>(src, g, idx, rho_out, U_out, T_out, partials);
+    moments_fp32_forms<M, S>(src, g, idx, end, block, rho_out, U_out, T_out, partials);
     return;
-  } else if (idx < g.ncell) {
+  } else if (idx < end) {
     double r = 0, mx = 0, my = 0, mz = 0, e2 = 0, mn = 1e300, bad = 0;
     sfor<0, Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
@@ -1034,7 +1067,7 @@ __global__ void __launch_bounds__(kMomentThreads, MomMinBlocks<S>::value)
     const int k = threadIdx.x;
     double v = sh[0][k];
     for (int w = 1; w < kMomentThreads / 32; ++w) v = (k == 5) ? fmin(v, sh[w][k]) : v + sh[w][k];
-    partials[(size_t)blockIdx.x * kAuditSlots + k] = v;
+    partials[(size_t)block * kAuditSlots + k] = v;
   }
 }
 

@@ -202,6 +202,7 @@ bool build_host_model(int model, HostModel* hm) {
     mc.X2[g] = a * a * vs.e2[g];
     mc.Wf[g] = (float)mc.W[g];
     mc.X2f[g] = (float)mc.X2[g];
+    mc.X2lo[g] = (float)(mc.X2[g] - (double)mc.X2f[g]);
   }
   for (int i = 0; i < vs.Q; ++i) {
     mc.w[i] = hm->w[i];
@@ -212,10 +213,12 @@ bool build_host_model(int model, HostModel* hm) {
   }
   mc.a = a;
   mc.af = (float)a;
+  mc.alo = (float)(a - (double)mc.af);
   mc.c = hm->c;
   mc.T0 = 1.0 / (2.0 * hm->c * hm->c);
   mc.T0f = (float)mc.T0;
   mc.iT0f = (float)(2.0 * hm->c * hm->c);
+  mc.iT0lo = (float)(2.0 * hm->c * hm->c - (double)mc.iT0f);
   return hm->residual < 1e-13;
 }
 
@@ -371,10 +374,19 @@ struct StepGraph {
   }
 };
 
+// lbm_init from host fields uploads in chunks on a second stream, so that the copy of
+// chunk k + 1 overlaps the check and equilibrium kernels of chunk k (below this many
+// cells: one chunk).
+constexpr int kXferChunks = 8;
+constexpr long long kXferMinCells = 1 << 20;
+
 struct lbm_ctx {
   ~lbm_ctx() {
     graph.reset();
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    for (cudaEvent_t& e : xfer_ev)
+      if (e) cudaEventDestroy(e);
+    if (xfer_stream) cudaStreamDestroy(xfer_stream);
   }
   int model = 0, storage = 0, dev = 0, D = 0, Q = 0;
   const StorageOps* ops = nullptr;
@@ -401,6 +413,8 @@ struct lbm_ctx {
   int graph_steps = kGraphSteps;   // 0: launch every step directly
   StepGraph graph;
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t xfer_stream = nullptr;          // chunked host uploads (lbm_init)
+  cudaEvent_t xfer_ev[kXferChunks + 1] = {};   // per chunk, and the start
   int64_t audit_every = 0;         // lbm_step audits after every multiple of this many steps
   double audit_host[kAuditSlots] = {0};
   // slab of a decomposed grid (lbm_create_slab): split axis (2 z, 1 y; -1 none),
@@ -773,7 +787,8 @@ int lbm_set_fixed_ends(lbm_ctx* c, int axis, int width, const double* lo, const 
                            cudaMemcpyHostToDevice, c->stream));
   Grid t{2, 1, 1, 2, 2};
   const double* f = static_cast<const double*>(fields.p);
-  cudaError_t e = c->ops->init(c->model, f, f + 2, f + 2 + 2 * D, c->fix_tmpl.p, t, c->stream);
+  cudaError_t e = c->ops->init(c->model, f, f + 2, f + 2 + 2 * D, c->fix_tmpl.p, t, 0, t.ncell,
+                               c->stream);
   if (e != cudaSuccess) return cuda_fail(e, "end-state equilibrium launch");
   LBM_CUDA(cudaStreamSynchronize(c->stream));
   c->launches += 1;
@@ -790,6 +805,17 @@ int lbm_set_stream(lbm_ctx* c, void* stream) {
   return LBM_OK;
 }
 
+// The copy stream and its events (created on first use).
+static int ensure_xfer(lbm_ctx* c) {
+  if (!c->xfer_stream &&
+      cudaStreamCreateWithFlags(&c->xfer_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(LBM_ECUDA, "cannot create the copy stream");
+  for (cudaEvent_t& ev : c->xfer_ev)
+    if (!ev && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+      return fail(LBM_ECUDA, "cannot create the copy events");
+  return LBM_OK;
+}
+
 int lbm_init(lbm_ctx* c, const double* rho, const double* U, const double* T, int where) {
   if (!c) return fail(LBM_EINVAL, "ctx is NULL");
   if (!rho || !U || !T) return fail(LBM_EINVAL, "rho, U and T are required");
@@ -799,21 +825,54 @@ int lbm_init(lbm_ctx* c, const double* rho, const double* U, const double* T, in
   int rc = c->fields.ensure((size_t)(c->D + 2) * n * sizeof(double), c->stream);
   if (rc) return rc;
   double* f = static_cast<double*>(c->fields.p);
-  const cudaMemcpyKind kind = where == LBM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-  LBM_CUDA(cudaMemcpyAsync(f, rho, n * sizeof(double), kind, c->stream));
-  LBM_CUDA(cudaMemcpyAsync(f + n, U, (size_t)c->D * n * sizeof(double), kind, c->stream));
-  LBM_CUDA(cudaMemcpyAsync(f + (size_t)(c->D + 1) * n, T, n * sizeof(double), kind, c->stream));
-  if (where == LBM_HOST) {
-    // host fields are validated on the device once uploaded (a pass over them on the
-    // host costs more than the upload), before the equilibrium is launched
-    if ((rc = c->check.ensure(sizeof(unsigned long long), c->stream))) return rc;
-    LBM_CUDA(cudaMemsetAsync(c->check.p, 0xff, sizeof(unsigned long long), c->stream));
-    cudaError_t e = launch_check_fields(f, f + n, f + (size_t)(c->D + 1) * n, (long long)n, c->D,
-                                        static_cast<unsigned long long*>(c->check.p), c->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "field check launch");
+  double* fU = f + n;
+  double* fT = f + (size_t)(c->D + 1) * n;
+  if (where == LBM_DEVICE) {
+    LBM_CUDA(cudaMemcpyAsync(f, rho, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    LBM_CUDA(cudaMemcpyAsync(fU, U, (size_t)c->D * n * sizeof(double), cudaMemcpyDeviceToDevice,
+                             c->stream));
+    LBM_CUDA(cudaMemcpyAsync(fT, T, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    c->cur = 0;
+    cudaError_t e = c->ops->init(c->model, f, fU, fT, c->state[0].p, c->g, 0, (long long)n,
+                                 c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "init launch");
     c->launches += 1;
+  } else {
+    // Host fields: uploaded in chunks on the copy stream; chunk k's check and
+    // equilibrium run on the context's stream once its copies have landed, while the
+    // next chunk uploads.  The equilibrium goes to the buffer that does not hold the
+    // live state, which becomes live only once every value has passed the check
+    // (the fields are validated on the device: a pass over them on the host costs
+    // more than the upload).
+    if ((rc = c->check.ensure(sizeof(unsigned long long), c->stream))) return rc;
+    if ((rc = ensure_xfer(c))) return rc;
+    const int spare = c->inited ? (c->cur ^ 1) : 0;
+    unsigned long long* bad_d = static_cast<unsigned long long*>(c->check.p);
+    LBM_CUDA(cudaMemsetAsync(bad_d, 0xff, sizeof(unsigned long long), c->stream));
+    // the copies overwrite the fields buffer only after the work queued before this call
+    LBM_CUDA(cudaEventRecord(c->xfer_ev[kXferChunks], c->stream));
+    LBM_CUDA(cudaStreamWaitEvent(c->xfer_stream, c->xfer_ev[kXferChunks], 0));
+    const int nch = (long long)n >= kXferMinCells ? kXferChunks : 1;
+    for (int k = 0; k < nch; ++k) {
+      const size_t a = n * (size_t)k / (size_t)nch, b = n * (size_t)(k + 1) / (size_t)nch;
+      const size_t bytes = (b - a) * sizeof(double);
+      LBM_CUDA(cudaMemcpyAsync(f + a, rho + a, bytes, cudaMemcpyHostToDevice, c->xfer_stream));
+      for (int d = 0; d < c->D; ++d)
+        LBM_CUDA(cudaMemcpyAsync(fU + (size_t)d * n + a, U + (size_t)d * n + a, bytes,
+                                 cudaMemcpyHostToDevice, c->xfer_stream));
+      LBM_CUDA(cudaMemcpyAsync(fT + a, T + a, bytes, cudaMemcpyHostToDevice, c->xfer_stream));
+      LBM_CUDA(cudaEventRecord(c->xfer_ev[k], c->xfer_stream));
+      LBM_CUDA(cudaStreamWaitEvent(c->stream, c->xfer_ev[k], 0));
+      cudaError_t e = launch_check_fields(f, fU, fT, (long long)n, (long long)a, (long long)b,
+                                          c->D, bad_d, c->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "field check launch");
+      e = c->ops->init(c->model, f, fU, fT, c->state[spare].p, c->g, (long long)a, (long long)b,
+                       c->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "init launch");
+      c->launches += 2;
+    }
     unsigned long long bad = 0;
-    LBM_CUDA(cudaMemcpyAsync(&bad, c->check.p, sizeof bad, cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(cudaMemcpyAsync(&bad, bad_d, sizeof bad, cudaMemcpyDeviceToHost, c->stream));
     LBM_CUDA(cudaStreamSynchronize(c->stream));
     if (bad != ~0ull) {
       c->rec.valid = false;   // the kept initial fields were overwritten
@@ -824,12 +883,8 @@ int lbm_init(lbm_ctx* c, const double* rho, const double* U, const double* T, in
         default: return fail(LBM_EINVAL, "U has a non-finite value at cell %zu", k);
       }
     }
+    c->cur = spare;
   }
-  c->cur = 0;
-  cudaError_t e = c->ops->init(c->model, f, f + n, f + (size_t)(c->D + 1) * n, c->state[0].p, c->g,
-                               c->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "init launch");
-  c->launches += 1;
   c->inited = true;
   c->steps = 0;
   c->rec.valid = false;
@@ -839,7 +894,8 @@ int lbm_init(lbm_ctx* c, const double* rho, const double* U, const double* T, in
 // The conservation audit of the current state into c->audit_host (blocking).
 int run_audit(lbm_ctx* c) {
   cudaError_t e = c->ops->moments(c->model, c->state[c->cur].p, c->g, nullptr, nullptr, nullptr,
-                                  static_cast<double*>(c->partials.p), c->stream);
+                                  static_cast<double*>(c->partials.p), 0,
+                                  moment_blocks(c->g.ncell), c->stream);
   if (e != cudaSuccess) return cuda_fail(e, "audit launch");
   e = launch_audit_reduce(static_cast<double*>(c->partials.p), moment_blocks(c->g.ncell),
                           static_cast<double*>(c->audit_out.p), c->stream);
@@ -994,24 +1050,51 @@ int lbm_moments(lbm_ctx* c, double* rho, double* U, double* T, int where) {
   DeviceGuard dg(c->dev);
   const size_t n = (size_t)c->g.ncell;
   double *dr = rho, *du = U, *dt = T;
+  int rc = LBM_OK;
   if (where == LBM_HOST) {
-    int rc = c->mom.ensure((size_t)(c->D + 2) * n * sizeof(double), c->stream);
-    if (rc) return rc;
+    if ((rc = c->mom.ensure((size_t)(c->D + 2) * n * sizeof(double), c->stream))) return rc;
     double* m = static_cast<double*>(c->mom.p);
     dr = rho ? m : nullptr;
     du = U ? m + n : nullptr;
     dt = T ? m + (size_t)(c->D + 1) * n : nullptr;
   }
-  cudaError_t e = c->ops->moments(c->model, c->state[c->cur].p, c->g, dr, du, dt,
-                                  static_cast<double*>(c->partials.p), c->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "moments launch");
-  c->launches += 1;
-  if (where == LBM_HOST) {
-    if (rho) LBM_CUDA(cudaMemcpyAsync(rho, dr, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    if (U) LBM_CUDA(cudaMemcpyAsync(U, du, (size_t)c->D * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    if (T) LBM_CUDA(cudaMemcpyAsync(T, dt, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    LBM_CUDA(cudaStreamSynchronize(c->stream));
+  if (where == LBM_DEVICE) {
+    cudaError_t e = c->ops->moments(c->model, c->state[c->cur].p, c->g, dr, du, dt,
+                                    static_cast<double*>(c->partials.p), 0,
+                                    moment_blocks(c->g.ncell), c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "moments launch");
+    c->launches += 1;
+    return LBM_OK;
   }
+  // Host outputs: the moments in chunks on the context's stream, each chunk read back
+  // on the copy stream while the next one is computed.
+  if ((rc = ensure_xfer(c))) return rc;
+  const long long nb = moment_blocks(c->g.ncell);
+  const int nch = (long long)n >= kXferMinCells ? kXferChunks : 1;
+  for (int k = 0; k < nch; ++k) {
+    const long long b0 = nb * k / nch, b1 = nb * (k + 1) / nch;
+    cudaError_t e = c->ops->moments(c->model, c->state[c->cur].p, c->g, dr, du, dt,
+                                    static_cast<double*>(c->partials.p), b0, b1 - b0, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "moments launch");
+    c->launches += 1;
+    LBM_CUDA(cudaEventRecord(c->xfer_ev[k], c->stream));
+    LBM_CUDA(cudaStreamWaitEvent(c->xfer_stream, c->xfer_ev[k], 0));
+    const size_t a = (size_t)b0 * kMomentThreads;
+    const size_t b = std::min(n, (size_t)b1 * kMomentThreads);
+    const size_t bytes = (b - a) * sizeof(double);
+    if (rho)
+      LBM_CUDA(cudaMemcpyAsync(rho + a, dr + a, bytes, cudaMemcpyDeviceToHost, c->xfer_stream));
+    if (U)
+      for (int d = 0; d < c->D; ++d)
+        LBM_CUDA(cudaMemcpyAsync(U + (size_t)d * n + a, du + (size_t)d * n + a, bytes,
+                                 cudaMemcpyDeviceToHost, c->xfer_stream));
+    if (T) LBM_CUDA(cudaMemcpyAsync(T + a, dt + a, bytes, cudaMemcpyDeviceToHost, c->xfer_stream));
+  }
+  // the context's stream resumes once the read-back is complete (the staging buffer
+  // is free again), and the call returns with the host arrays filled
+  LBM_CUDA(cudaEventRecord(c->xfer_ev[kXferChunks], c->xfer_stream));
+  LBM_CUDA(cudaStreamWaitEvent(c->stream, c->xfer_ev[kXferChunks], 0));
+  LBM_CUDA(cudaStreamSynchronize(c->xfer_stream));
   return LBM_OK;
 }
 

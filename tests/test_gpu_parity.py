@@ -245,6 +245,39 @@ def test_errors_are_reported_before_launch(lbm):
         assert ei.value.code == lbm.LBM_EINVAL and name in str(ei.value)
 
 
+def test_chunked_host_init(lbm):
+    """Host fields on a grid of at least 2^20 cells are uploaded, checked and turned
+    into their equilibrium in 8 chunks: the state equals the one made from the same
+    fields on the device (bitwise), and a bad value in the last chunk is refused
+    with the previous state left live."""
+    import torch
+    dims = (128, 96, 96)   # 1,179,648 cells
+    shape = dims[::-1]
+    rng = np.random.default_rng(9)
+    rho = 1.0 + 0.05 * rng.uniform(-1, 1, shape)
+    U = 0.05 * rng.uniform(-1, 1, (3,) + shape)
+    lat = lbm.Lattice("D3Q95", dims, 1.6, "fp32")
+    T = (1.0 + 0.05 * rng.uniform(-1, 1, shape)) * lat.info["T0"]
+    dev = lbm.Lattice("D3Q95", dims, 1.6, "fp32")
+    try:
+        lat.init(rho, U, T)
+        dev.init(torch.from_numpy(rho).cuda(), torch.from_numpy(U).cuda(), torch.from_numpy(T).cuda())
+        assert np.array_equal(lat.raw().view(np.uint32), dev.raw().view(np.uint32))
+        lat.step(3)
+        before = lat.raw()
+        bad = T.copy()
+        bad.reshape(-1)[-7] = -1.0
+        with pytest.raises(lbm.LbmError) as ei:
+            lat.init(rho, U, bad)
+        assert ei.value.code == lbm.LBM_EINVAL and "T[%d]" % (rho.size - 7) in str(ei.value)
+        assert np.array_equal(lat.raw().view(np.uint32), before.view(np.uint32))
+        assert lbm.lbm_steps_done(lat.ctx) == 3
+        lat.step(1)
+    finally:
+        lat.close()
+        dev.close()
+
+
 def test_grid_and_argument_limits(lbm):
     """Empty, oversized and malformed grids and arguments are refused on the host
     (nothing is allocated or launched); zero steps is a no-op."""
