@@ -701,6 +701,7 @@ int lbm_destroy(lbm_ctx* c) {
   if (!c) return LBM_OK;
   DeviceGuard dg(c->dev);
   cudaStreamSynchronize(c->stream);
+  if (c->xfer_stream) cudaStreamSynchronize(c->xfer_stream);
   delete c;
   return LBM_OK;
 }
