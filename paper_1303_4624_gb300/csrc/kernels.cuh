@@ -741,13 +741,13 @@ __global__ void __launch_bounds__(kSplitThreads, LBM_SPLIT_MINB)
 
 // ----------------------------------------------------------------- equilibrium init
 // h_i = rho P_i(u, theta) - 1 for the fields rho, U (lattice), T (lattice) of each cell,
-// rounded once to the storage type.  FP64, or (FP32 storage) double-float on the
-// FP32 pipe, whose ~48 significant bits round to the same FP32 value as FP64 except
-// within 2^-44 relative of a rounding boundary.  The FP32 form splits its five FP64
-// inputs into double-float once and does everything else on the FP32 pipe: on this
-// GPU the FP64 pipe issues 1/64 of the FP32 rate, and the FP64 form of the 95
-// direction polynomials is bound by it (~38 ms for 33.5 M cells; with the shell
-// coefficients alone in FP64, ~13 ms).
+// rounded once to the storage type.  FP64 for the FP64 form; double-float on the FP32
+// pipe for the FP32, FP16 and BF16 forms, whose ~48 significant bits round to the
+// same value as FP64 except within 2^-44 relative of a rounding boundary.  The five
+// FP64 inputs are split into double-float once and everything else runs on the FP32
+// pipe: on this GPU the FP64 pipe issues 1/64 of the FP32 rate, and the FP64 form of
+// the 95 direction polynomials is bound by it (~38 ms for 33.5 M cells; with the
+// shell coefficients alone in FP64, ~13 ms; all in double-float, 6.7 ms).
 
 // double-float helpers (FMA products, Knuth / Dekker sums; see ff_add)
 __device__ __forceinline__ FF ff_from(double d) {
@@ -781,6 +781,34 @@ __device__ __forceinline__ FF ff_scale(FF a) {
 __device__ __forceinline__ FF ff_neg(FF a) { return {-a.hi, -a.lo}; }
 __device__ __forceinline__ FF ff_const(float c) { return {c, 0.f}; }
 
+// hi + lo rounded once to the storage type.  FP32: one add.  FP16 / BF16: round hi,
+// unless hi is exactly halfway between two neighbours of the 16-bit format (FP32
+// holds those midpoints exactly), where the sign of lo decides; since hi is hi + lo
+// rounded to FP32, no other case can put hi and hi + lo on opposite sides of a
+// midpoint.
+template <class S>
+__device__ __forceinline__ S ff_round(FF v);
+template <>
+__device__ __forceinline__ float ff_round<float>(FF v) {
+  return __fadd_rn(v.hi, v.lo);
+}
+template <>
+__device__ __forceinline__ __half ff_round<__half>(FF v) {
+  const __half a = __float2half_rd(v.hi), b = __float2half_ru(v.hi);
+  if (v.lo != 0.f && __half_as_ushort(a) != __half_as_ushort(b) &&
+      v.hi == 0.5f * (__half2float(a) + __half2float(b)))
+    return v.lo > 0.f ? b : a;
+  return __float2half_rn(v.hi);
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 ff_round<__nv_bfloat16>(FF v) {
+  const __nv_bfloat16 a = __float2bfloat16_rd(v.hi), b = __float2bfloat16_ru(v.hi);
+  if (v.lo != 0.f && __bfloat16_as_ushort(a) != __bfloat16_as_ushort(b) &&
+      v.hi == 0.5f * (__bfloat162float(a) + __bfloat162float(b)))
+    return v.lo > 0.f ? b : a;
+  return __float2bfloat16_rn(v.hi);
+}
+
 // s = e . (a u) as double-float for a compile-time lattice vector e
 template <int EX, int EY, int EZ>
 __device__ __forceinline__ FF ff_edot(FF vx, FF vy, FF vz) {
@@ -803,7 +831,7 @@ __global__ void __launch_bounds__(256)
   const ModelConst& mc = c_mc[M];
   const long long idx = begin + (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= end) return;
-  if constexpr (std::is_same<S, float>::value) {
+  if constexpr (!std::is_same<S, double>::value) {
     // the coefficients of EqCoef (see there), with rho folded in per shell:
     //   h_i = (rho - 1) + rho (A0 - 1) + rho A2 s^2 + rho s^4 / 24 + s (rho A1 + rho s^2 / 6)
     constexpr double kSixth = 1.0 / 6.0, kTwentyFourth = 1.0 / 24.0;
@@ -832,7 +860,7 @@ __global__ void __launch_bounds__(256)
     const FF r6 = ff_mul(r, FF{c6h, c6l}), r24 = ff_mul(r, FF{c24h, c24l});
     {
       const FF h0 = ff_add(rm1, ff_mul(r, K0m1));
-      dst[idx] = __fadd_rn(h0.hi, h0.lo);   // one rounding to FP32
+      dst[idx] = ff_round<S>(h0);   // one rounding to the storage type
     }
     FF R0 = {0.f, 0.f}, R1 = R0, R2 = R0;
     sfor<0, NP>([&](auto P) {
@@ -854,8 +882,8 @@ __global__ void __launch_bounds__(256)
       const FF od = ff_mul(s, ff_add(R1, ff_mul(s2, r6)));
       const FF hp = ff_add(ev, od);
       const FF hm = ff_add(ev, ff_neg(od));
-      dst[(size_t)ip * g.ncell + idx] = __fadd_rn(hp.hi, hp.lo);   // one rounding to FP32
-      dst[(size_t)im * g.ncell + idx] = __fadd_rn(hm.hi, hm.lo);
+      dst[(size_t)ip * g.ncell + idx] = ff_round<S>(hp);
+      dst[(size_t)im * g.ncell + idx] = ff_round<S>(hm);
     });
     return;
   }
