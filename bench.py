@@ -353,7 +353,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def e2e_leg(lbm, W, wl, fields, steps, stream, reps=3):
+def e2e_leg(lbm, W, wl, fields, steps, stream, reps=5):
     """Whole job through the public API from pinned host buffers: lbm_init from
     host fields, `steps` steps, lbm_moments back to host; timed on the host clock."""
     import numpy as np
