@@ -77,6 +77,13 @@ __device__ __forceinline__ double block_sum_128(double v, double* sh) {
 #ifndef LBM_ADJ_MINB
 #define LBM_ADJ_MINB 4
 #endif
+// The FP32 adjoint commits its lambda copies in this many groups and waits for each
+// just before pass 1 needs it, so the later groups' latency overlaps pass 1 (1.75
+// adjoint steps per forward step against 1.78 with one wait for all; 2, 3 or 6
+// groups measured 1.76).
+#ifndef LBM_ADJ_GROUPS
+#define LBM_ADJ_GROUPS 4
+#endif
 #ifndef LBM_ADJ_LAM_SMEM
 #define LBM_ADJ_LAM_SMEM 1
 #endif
@@ -114,6 +121,10 @@ __global__ void __launch_bounds__(kAdjThreads, AdjMinBlocks<S>::value)
   using Rt = L;
   constexpr int Q = Mo::Q, D = Mo::D, RR = Mo::R, NP = Mo::NP;
   constexpr bool kSm = AdjLamSmem<L>::value;
+  // the lambda copies are committed in kGroups groups of kPerGroup pairs; pass 1
+  // waits for each group just before its first pair
+  constexpr int kGroups = LBM_ADJ_GROUPS;
+  constexpr int kPerGroup = (NP + kGroups - 1) / kGroups;
   const ModelConst& mc = c_mc[M];
   __shared__ double sh[4];
   extern __shared__ __align__(16) unsigned char adj_dyn[];
@@ -152,13 +163,16 @@ __global__ void __launch_bounds__(kAdjThreads, AdjMinBlocks<S>::value)
         const int cp = zo[RR - ez] + yo[RR - ey] + xo[RR - ex];   // x + e_ip
         cp_async4(dst + ip * kAdjThreads, LBM_POP(nu_next, ip, cp));
         cp_async4(dst + im * kAdjThreads, LBM_POP(nu_next, im, cm));
+        if constexpr (kGroups > 1 && (p % kPerGroup == kPerGroup - 1 || p + 1 == NP))
+          cp_async_commit();
       });
-      cp_async_wait_all();
+      if constexpr (kGroups <= 1) cp_async_wait_all();
     }
     // pass 1: forward moments of g (gathered from x - e_i) and sum lambda_i f_i
     Rt rs, es = Rt(0), jx = Rt(0), jy = Rt(0), jz = Rt(0), sg;
     {
       const Rt h0 = (Rt)Codec<S>::ld(state + self);
+      if constexpr (kSm && !kFirst && kGroups > 1) cp_async_wait_group<kGroups - 1>();
       if constexpr (!kSm && !kFirst) lam_r[0] = nu_next[self];
       rs = gW<Rt>(mc, 0) * h0;
       sg = gW<Rt>(mc, 0) * lam(0) * (Rt(1) + h0);
@@ -173,6 +187,8 @@ __global__ void __launch_bounds__(kAdjThreads, AdjMinBlocks<S>::value)
       constexpr int ex = Mo::vs.e[ip][0], ey = Mo::vs.e[ip][1], ez = Mo::vs.e[ip][2];
       constexpr bool first = (p == 0) || (Mo::vs.grp[ip - 2] != gg);
       constexpr bool last = (p + 1 == NP) || (Mo::vs.grp[ip + 2] != gg);
+      if constexpr (kSm && !kFirst && kGroups > 1 && p > 0 && p % kPerGroup == 0)
+        cp_async_wait_group<kGroups - 1 - p / kPerGroup>();
       const int cm = zo[ez + RR] + yo[ey + RR] + xo[ex + RR];   // x - e_ip
       const int cp = zo[RR - ez] + yo[RR - ey] + xo[RR - ex];   // x + e_ip
       const Rt hp = (Rt)Codec<S>::ld(LBM_POP(state, ip, cm));

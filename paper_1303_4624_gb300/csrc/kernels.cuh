@@ -589,6 +589,15 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
+// Close the group of this thread's cp.async copies issued since the last commit, and
+// wait until at most N of its committed groups are still in flight.
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 // Launched with programmatic stream serialization: the next step's grid may be
 // scheduled while this one drains; griddepcontrol.wait holds every thread until
