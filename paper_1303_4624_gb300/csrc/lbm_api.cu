@@ -817,6 +817,37 @@ static int ensure_xfer(lbm_ctx* c) {
   return LBM_OK;
 }
 
+// lbm_init's chunked upload of host fields (see lbm_init): copies on the copy stream,
+// each chunk's field check and equilibrium (into state[spare]) on the context's
+// stream after its copies.
+static int upload_and_init(lbm_ctx* c, const double* rho, const double* U, const double* T,
+                           int spare, unsigned long long* bad_d) {
+  const size_t n = (size_t)c->g.ncell;
+  double* f = static_cast<double*>(c->fields.p);
+  double* fU = f + n;
+  double* fT = f + (size_t)(c->D + 1) * n;
+  const int nch = (long long)n >= kXferMinCells ? kXferChunks : 1;
+  for (int k = 0; k < nch; ++k) {
+    const size_t a = n * (size_t)k / (size_t)nch, b = n * (size_t)(k + 1) / (size_t)nch;
+    const size_t bytes = (b - a) * sizeof(double);
+    LBM_CUDA(cudaMemcpyAsync(f + a, rho + a, bytes, cudaMemcpyHostToDevice, c->xfer_stream));
+    for (int d = 0; d < c->D; ++d)
+      LBM_CUDA(cudaMemcpyAsync(fU + (size_t)d * n + a, U + (size_t)d * n + a, bytes,
+                               cudaMemcpyHostToDevice, c->xfer_stream));
+    LBM_CUDA(cudaMemcpyAsync(fT + a, T + a, bytes, cudaMemcpyHostToDevice, c->xfer_stream));
+    LBM_CUDA(cudaEventRecord(c->xfer_ev[k], c->xfer_stream));
+    LBM_CUDA(cudaStreamWaitEvent(c->stream, c->xfer_ev[k], 0));
+    cudaError_t e = launch_check_fields(f, fU, fT, (long long)n, (long long)a, (long long)b, c->D,
+                                        bad_d, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "field check launch");
+    e = c->ops->init(c->model, f, fU, fT, c->state[spare].p, c->g, (long long)a, (long long)b,
+                     c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "init launch");
+    c->launches += 2;
+  }
+  return LBM_OK;
+}
+
 int lbm_init(lbm_ctx* c, const double* rho, const double* U, const double* T, int where) {
   if (!c) return fail(LBM_EINVAL, "ctx is NULL");
   if (!rho || !U || !T) return fail(LBM_EINVAL, "rho, U and T are required");
@@ -853,24 +884,12 @@ int lbm_init(lbm_ctx* c, const double* rho, const double* U, const double* T, in
     // the copies overwrite the fields buffer only after the work queued before this call
     LBM_CUDA(cudaEventRecord(c->xfer_ev[kXferChunks], c->stream));
     LBM_CUDA(cudaStreamWaitEvent(c->xfer_stream, c->xfer_ev[kXferChunks], 0));
-    const int nch = (long long)n >= kXferMinCells ? kXferChunks : 1;
-    for (int k = 0; k < nch; ++k) {
-      const size_t a = n * (size_t)k / (size_t)nch, b = n * (size_t)(k + 1) / (size_t)nch;
-      const size_t bytes = (b - a) * sizeof(double);
-      LBM_CUDA(cudaMemcpyAsync(f + a, rho + a, bytes, cudaMemcpyHostToDevice, c->xfer_stream));
-      for (int d = 0; d < c->D; ++d)
-        LBM_CUDA(cudaMemcpyAsync(fU + (size_t)d * n + a, U + (size_t)d * n + a, bytes,
-                                 cudaMemcpyHostToDevice, c->xfer_stream));
-      LBM_CUDA(cudaMemcpyAsync(fT + a, T + a, bytes, cudaMemcpyHostToDevice, c->xfer_stream));
-      LBM_CUDA(cudaEventRecord(c->xfer_ev[k], c->xfer_stream));
-      LBM_CUDA(cudaStreamWaitEvent(c->stream, c->xfer_ev[k], 0));
-      cudaError_t e = launch_check_fields(f, fU, fT, (long long)n, (long long)a, (long long)b,
-                                          c->D, bad_d, c->stream);
-      if (e != cudaSuccess) return cuda_fail(e, "field check launch");
-      e = c->ops->init(c->model, f, fU, fT, c->state[spare].p, c->g, (long long)a, (long long)b,
-                       c->stream);
-      if (e != cudaSuccess) return cuda_fail(e, "init launch");
-      c->launches += 2;
+    if ((rc = upload_and_init(c, rho, U, T, spare, bad_d))) {
+      // nothing may still read the caller's arrays once the call has returned
+      c->rec.valid = false;
+      cudaStreamSynchronize(c->xfer_stream);
+      cudaStreamSynchronize(c->stream);
+      return rc;
     }
     unsigned long long bad = 0;
     LBM_CUDA(cudaMemcpyAsync(&bad, bad_d, sizeof bad, cudaMemcpyDeviceToHost, c->stream));
@@ -1044,6 +1063,39 @@ int lbm_load(lbm_ctx* c, const char* path) {
 int64_t lbm_steps_done(const lbm_ctx* c) { return c ? c->steps : -1; }
 int64_t lbm_launch_count(const lbm_ctx* c) { return c ? c->launches : -1; }
 
+// lbm_moments' chunked read-back to host arrays (see lbm_moments); dr, du, dt are the
+// device staging arrays.
+static int moments_to_host(lbm_ctx* c, double* rho, double* U, double* T, double* dr, double* du,
+                           double* dt) {
+  const size_t n = (size_t)c->g.ncell;
+  const long long nb = moment_blocks(c->g.ncell);
+  const int nch = (long long)n >= kXferMinCells ? kXferChunks : 1;
+  for (int k = 0; k < nch; ++k) {
+    const long long b0 = nb * k / nch, b1 = nb * (k + 1) / nch;
+    cudaError_t e = c->ops->moments(c->model, c->state[c->cur].p, c->g, dr, du, dt,
+                                    static_cast<double*>(c->partials.p), b0, b1 - b0, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "moments launch");
+    c->launches += 1;
+    LBM_CUDA(cudaEventRecord(c->xfer_ev[k], c->stream));
+    LBM_CUDA(cudaStreamWaitEvent(c->xfer_stream, c->xfer_ev[k], 0));
+    const size_t a = (size_t)b0 * kMomentThreads;
+    const size_t b = std::min(n, (size_t)b1 * kMomentThreads);
+    const size_t bytes = (b - a) * sizeof(double);
+    if (rho)
+      LBM_CUDA(cudaMemcpyAsync(rho + a, dr + a, bytes, cudaMemcpyDeviceToHost, c->xfer_stream));
+    if (U)
+      for (int d = 0; d < c->D; ++d)
+        LBM_CUDA(cudaMemcpyAsync(U + (size_t)d * n + a, du + (size_t)d * n + a, bytes,
+                                 cudaMemcpyDeviceToHost, c->xfer_stream));
+    if (T) LBM_CUDA(cudaMemcpyAsync(T + a, dt + a, bytes, cudaMemcpyDeviceToHost, c->xfer_stream));
+  }
+  // the context's stream resumes once the read-back is complete (the staging buffer is
+  // free again)
+  LBM_CUDA(cudaEventRecord(c->xfer_ev[kXferChunks], c->xfer_stream));
+  LBM_CUDA(cudaStreamWaitEvent(c->stream, c->xfer_ev[kXferChunks], 0));
+  return LBM_OK;
+}
+
 int lbm_moments(lbm_ctx* c, double* rho, double* U, double* T, int where) {
   if (!c) return fail(LBM_EINVAL, "ctx is NULL");
   if (!c->inited) return fail(LBM_ESTATE, "lbm_moments before lbm_init");
@@ -1070,33 +1122,10 @@ int lbm_moments(lbm_ctx* c, double* rho, double* U, double* T, int where) {
   // Host outputs: the moments in chunks on the context's stream, each chunk read back
   // on the copy stream while the next one is computed.
   if ((rc = ensure_xfer(c))) return rc;
-  const long long nb = moment_blocks(c->g.ncell);
-  const int nch = (long long)n >= kXferMinCells ? kXferChunks : 1;
-  for (int k = 0; k < nch; ++k) {
-    const long long b0 = nb * k / nch, b1 = nb * (k + 1) / nch;
-    cudaError_t e = c->ops->moments(c->model, c->state[c->cur].p, c->g, dr, du, dt,
-                                    static_cast<double*>(c->partials.p), b0, b1 - b0, c->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "moments launch");
-    c->launches += 1;
-    LBM_CUDA(cudaEventRecord(c->xfer_ev[k], c->stream));
-    LBM_CUDA(cudaStreamWaitEvent(c->xfer_stream, c->xfer_ev[k], 0));
-    const size_t a = (size_t)b0 * kMomentThreads;
-    const size_t b = std::min(n, (size_t)b1 * kMomentThreads);
-    const size_t bytes = (b - a) * sizeof(double);
-    if (rho)
-      LBM_CUDA(cudaMemcpyAsync(rho + a, dr + a, bytes, cudaMemcpyDeviceToHost, c->xfer_stream));
-    if (U)
-      for (int d = 0; d < c->D; ++d)
-        LBM_CUDA(cudaMemcpyAsync(U + (size_t)d * n + a, du + (size_t)d * n + a, bytes,
-                                 cudaMemcpyDeviceToHost, c->xfer_stream));
-    if (T) LBM_CUDA(cudaMemcpyAsync(T + a, dt + a, bytes, cudaMemcpyDeviceToHost, c->xfer_stream));
-  }
-  // the context's stream resumes once the read-back is complete (the staging buffer
-  // is free again), and the call returns with the host arrays filled
-  LBM_CUDA(cudaEventRecord(c->xfer_ev[kXferChunks], c->xfer_stream));
-  LBM_CUDA(cudaStreamWaitEvent(c->stream, c->xfer_ev[kXferChunks], 0));
-  LBM_CUDA(cudaStreamSynchronize(c->xfer_stream));
-  return LBM_OK;
+  rc = moments_to_host(c, rho, U, T, dr, du, dt);
+  // returns once the host arrays are filled (or, after an error, no longer written)
+  cudaStreamSynchronize(c->xfer_stream);
+  return rc;
 }
 
 int lbm_audit(lbm_ctx* c, double out[8]) {
