@@ -13,7 +13,8 @@ over the CUDA-event time of a launch, against the measured HBM copy bandwidth.
 Secondary measurements in the same line: the 128 x 64 x 64 planar Riemann setup
 (a 199 MB state, partly served from L2), the FP32 / FP16 / BF16 storage forms on
 the 512 x 256 x 256 grid, the cost of the adjoint relative to the forward on the
-128^3 adjoint workload, the 768 x 384 x 384 FP16 oblique problem, an end-to-end run
+128^3 adjoint workload, the 768 x 384 x 384 FP16 oblique problem (undivided, and as
+two slabs with halo messages on this one GPU), an end-to-end run
 through the public API from host buffers, and the FP64 oracle timed on the host
 cores (cpu_baseline).
 
@@ -21,8 +22,9 @@ cores (cpu_baseline).
 bounded sub-box sample of the same workload per step and prints the same JSON keys.
 
 Multi-GPU (torchrun, N > 1): every rank runs an independent replica of the
-workload (the path has no multi-GPU decomposition here: replicas only, weak
-scaling); the time is the maximum over ranks.
+workload (replicas only, weak scaling); the time is the maximum over ranks.  The
+slab decomposition of the library is timed on one GPU (the `slabs` leg: two slabs
+of the 768 x 384 x 384 FP16 workload with device-to-device halo messages).
 """
 from __future__ import annotations
 
@@ -59,6 +61,7 @@ def parse_args(argv=None):
                    help="stream-collide kernel of the timed workload (auto: the library's choice)")
     p.add_argument("--no-extras", action="store_true", help="skip the forms / adjoint / cpu legs")
     p.add_argument("--leg", default=None, choices=["forms", "adjoint", "large", "moments", "d2q33",
+                                                   "slabs",
                                                    "l2_assisted"],
                    help="run one secondary leg alone (for profiling) and print its JSON")
     return p.parse_args(argv)
@@ -257,7 +260,7 @@ def run_ours(args):
 
     stream = torch.cuda.current_stream()
     if args.leg:
-        fn = {"forms": forms_leg, "adjoint": adjoint_leg, "large": large_leg,
+        fn = {"forms": forms_leg, "adjoint": adjoint_leg, "large": large_leg, "slabs": slabs_leg,
               "moments": moments_leg, "d2q33": d2q33_leg, "l2_assisted": l2_assisted_leg}[args.leg]
         if rank == 0:
             print(json.dumps({"leg": args.leg, "result": fn(lbm, W, stream)}), flush=True)
@@ -345,6 +348,8 @@ def run_ours(args):
         del fields
         torch.cuda.empty_cache()
         line["large"] = large_leg(lbm, W, stream)
+        line["slabs"] = slabs_leg(lbm, W, stream,
+                                  undivided=line["large"].get("mlups") if line["large"] else None)
         line["cpu_baseline"] = cpu_baseline_leg()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -539,6 +544,49 @@ def large_leg(lbm, W, stream, steps=300):
     lbm.lbm_release_record(lat.ctx)
     lat.close()
     torch.cuda.empty_cache()
+    return out
+
+
+def slabs_leg(lbm, W, stream, undivided=None, nslabs=2, steps=20, warmup=3):
+    """The 768 x 384 x 384 FP16 oblique workload decomposed into z-slabs on this one
+    device (paper_1303_4624_gb300/slabs.py): every step advances each slab (interior
+    and ghost planes) and then packs and unpacks the halo messages of both faces of
+    every slab with device-to-device buffers.  MLUPS counts the grid's cells; against
+    the undivided grid's rate this is the cost of the ghost planes and the halo
+    kernels (the transport between GPUs is not part of it: one device)."""
+    import numpy as np
+    import torch
+    from paper_1303_4624_gb300 import slabs as SL
+    free, _ = torch.cuda.mem_get_info()
+    if free < 60e9:
+        return {"skipped": "needs 60 GB free device memory, %.0f GB free" % (free / 1e9)}
+    wl, fields = W.d3q95_oblique()
+    nz = wl.dims[2]
+    splits = [nz // nslabs + (1 if k < nz % nslabs else 0) for k in range(nslabs)]
+    sg = SL.SlabGrid(wl.model, wl.dims, wl.omega, wl.storage, splits)
+    try:
+        T0 = lbm.lbm_model_info(wl.model)["T0"]
+        sg.init(fields.rho, fields.U, fields.theta * T0)
+        del fields
+        sg.step(warmup)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        sg.step(steps)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        dt = ev[0].elapsed_time(ev[1]) / 1e3
+        h = lbm.lbm_halo_info(sg.ctxs[0])
+        ml = wl.cells * steps / dt / 1e6
+        out = {"workload": wl.name, "storage": wl.storage, "slabs": nslabs, "splits": splits,
+               "ghost_planes_per_side": h["ghost"], "face_bytes": h["face_bytes"],
+               "steps": steps, "mlups": round(ml, 1),
+               "of_undivided": None if not undivided else round(ml / undivided, 4),
+               "note": "all slabs on one GPU, halos by device-to-device buffers; MLUPS over "
+                       "the grid's cells"}
+    finally:
+        sg.close()
+        torch.cuda.empty_cache()
     return out
 
 
