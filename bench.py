@@ -341,7 +341,8 @@ def run_ours(args):
     torch.cuda.empty_cache()
     if rank == 0 and not args.no_extras:
         line["l2_assisted"] = l2_assisted_leg(lbm, W, stream)
-        line["e2e"] = e2e_leg(lbm, W, wl, fields, args.steps, stream)
+        line["e2e"] = e2e_leg(lbm, W, wl, fields, args.steps, stream,
+                              reps=5 if args.steps <= 1000 else 3)
         line["forms"] = forms_leg(lbm, W, stream)
         line["d2q33"] = d2q33_leg(lbm, W, stream)
         line["adjoint"] = adjoint_leg(lbm, W, stream)
