@@ -81,6 +81,12 @@ __device__ __forceinline__ double block_sum_128(double v, double* sh) {
 // just before pass 1 needs it, so the later groups' latency overlaps pass 1 (1.75
 // adjoint steps per forward step against 1.78 with one wait for all; 2, 3 or 6
 // groups measured 1.76).
+// Unroll factor of the shell loops of passes 2 and 3 (1.74 adjoint steps per forward
+// step at 2, 1.75 at 1, 1.78 at 3).
+#ifndef LBM_ADJ_UNROLL
+#define LBM_ADJ_UNROLL 2
+#endif
+constexpr int kAdjUnroll = LBM_ADJ_UNROLL;
 #ifndef LBM_ADJ_GROUPS
 #define LBM_ADJ_GROUPS 4
 #endif
@@ -254,7 +260,7 @@ __global__ void __launch_bounds__(kAdjThreads, AdjMinBlocks<S>::value)
         const Rt x2 = gX2<Rt>(mc, gg);
         const Rt A1 = cf.A1(x2), A2 = cf.A2(x2);
         m0 = m2 = m4 = n1 = n3 = gvx = gvy = gvz = Rt(0);
-#pragma unroll 1
+#pragma unroll kAdjUnroll
         for (int p = ShellPairs<M>::first(gg); p < ShellPairs<M>::end(gg); ++p) {
           const int ip = 1 + 2 * p, im = 2 + 2 * p;
           const Rt ex = mc.ef[ip][0], ey = mc.ef[ip][1], ez = mc.ef[ip][2];
@@ -342,7 +348,7 @@ __global__ void __launch_bounds__(kAdjThreads, AdjMinBlocks<S>::value)
       sfor<1, Mo::G>([&](auto Gi) {
         constexpr int gg = decltype(Gi)::value;
         const Rt ev = oa + og * gX2<Rt>(mc, gg);
-#pragma unroll 1
+#pragma unroll kAdjUnroll
         for (int p = ShellPairs<M>::first(gg); p < ShellPairs<M>::end(gg); ++p) {
           const int ip = 1 + 2 * p, im = 2 + 2 * p;
           const Rt od = mc.ef[ip][0] * obx + mc.ef[ip][1] * oby + mc.ef[ip][2] * obz;
