@@ -374,9 +374,9 @@ struct StepGraph {
   }
 };
 
-// lbm_init from host fields uploads in chunks on a second stream, so that the copy of
-// chunk k + 1 overlaps the check and equilibrium kernels of chunk k (below this many
-// cells: one chunk).
+// lbm_init from host fields and lbm_moments to host arrays move their data in chunks
+// on a second stream, so that the copy of one chunk overlaps the kernels of the next
+// (below this many cells: one chunk).
 constexpr int kXferChunks = 8;
 constexpr long long kXferMinCells = 1 << 20;
 
@@ -413,7 +413,7 @@ struct lbm_ctx {
   int graph_steps = kGraphSteps;   // 0: launch every step directly
   StepGraph graph;
   cudaStream_t cap_stream = nullptr;
-  cudaStream_t xfer_stream = nullptr;          // chunked host uploads (lbm_init)
+  cudaStream_t xfer_stream = nullptr;          // chunked host copies (lbm_init, lbm_moments)
   cudaEvent_t xfer_ev[kXferChunks + 1] = {};   // per chunk, and the start
   int64_t audit_every = 0;         // lbm_step audits after every multiple of this many steps
   double audit_host[kAuditSlots] = {0};
